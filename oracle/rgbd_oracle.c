@@ -1,0 +1,382 @@
+/*
+ * rgbd_oracle.c -- plain, slow, single-threaded CPU oracle for the depth-fused
+ * LBP + SVM hot path of "Robust real time face recognition and tracking on GPU
+ * using fusion of RGB and depth image" (Naik & Rathna, arXiv 1504.01883).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no source, header, table or constant generator
+ * with the CUDA library: every definition below is written out from the
+ * paper's text and the readings listed beside each function.
+ *
+ * Precision: the integer steps (resample, median, mask, LBP codes, histograms)
+ * are exact.  The per-cell normalisation has two forms: an fp64 one that feeds
+ * the fp64 SVM, and the fp32 IEEE quotient the fused kernel must reproduce
+ * bit for bit.  SVM scores are computed in fp64, directly from the definition
+ * (sum of squared differences, no norm expansion).
+ *
+ * Pins (what ties this file to something other than itself) live in
+ * tests/test_oracle_pins.py.  Every function here has at least one pin.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t frame, x, y, w, h;
+} orc_rect;
+
+/* ------------------------------------------------------------------ */
+/* S1. Affine resample (Section 2.1, Eq. 1: p' = x.u + y.v + t).       */
+/* ------------------------------------------------------------------ */
+
+/* floor(a / b) for b > 0, on int64. */
+static int64_t floor_div(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b != 0) && (a < 0)) q -= 1;
+    return q;
+}
+
+static int64_t clamp64(int64_t v, int64_t lo, int64_t hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/* Source coordinate (Q16.16) of crop pixel index i when a rect side starting
+ * at `origin` with length `len` is mapped onto `out_len` crop pixels, pixel
+ * centre to pixel centre:  origin + (i + 1/2) * len / out_len - 1/2.
+ * The fractional part is taken with floor division so CPU and GPU agree. */
+int64_t orc_rect_coord_q16(int32_t origin, int32_t len, int32_t out_len, int32_t i) {
+    int64_t num = (int64_t)(2 * (int64_t)i + 1) * (int64_t)len * 65536;
+    return (int64_t)origin * 65536 + floor_div(num, 2 * (int64_t)out_len) - 32768;
+}
+
+/* Bilinear sample of an 8-bit image at Q16.16 (Xq, Yq); taps clamped to the
+ * image (replicate edge), Q8 weights, result rounded half up. */
+uint8_t orc_bilinear_u8(const uint8_t* img, int H, int W, int64_t Xq, int64_t Yq) {
+    int64_t x0 = floor_div(Xq, 65536);
+    int64_t y0 = floor_div(Yq, 65536);
+    int64_t fx = (Xq - x0 * 65536) / 256; /* 0..255 */
+    int64_t fy = (Yq - y0 * 65536) / 256;
+    int64_t xa = clamp64(x0, 0, W - 1), xb = clamp64(x0 + 1, 0, W - 1);
+    int64_t ya = clamp64(y0, 0, H - 1), yb = clamp64(y0 + 1, 0, H - 1);
+    int64_t p00 = img[ya * W + xa], p01 = img[ya * W + xb];
+    int64_t p10 = img[yb * W + xa], p11 = img[yb * W + xb];
+    int64_t acc = (256 - fx) * (256 - fy) * p00 + fx * (256 - fy) * p01 +
+                  (256 - fx) * fy * p10 + fx * fy * p11;
+    return (uint8_t)((acc + 32768) / 65536);
+}
+
+/* Nearest-neighbour sample of a 16-bit depth image (never interpolated). */
+uint16_t orc_nearest_u16(const uint16_t* img, int H, int W, int64_t Xq, int64_t Yq) {
+    int64_t ix = clamp64(floor_div(Xq + 32768, 65536), 0, W - 1);
+    int64_t iy = clamp64(floor_div(Yq + 32768, 65536), 0, H - 1);
+    return img[iy * W + ix];
+}
+
+/* One crop.  With `affine` (6 x int32 Q16.16: a00 a01 t0 a10 a11 t1) the
+ * source point is Xq = a00*u + a01*v + t0, Yq = a10*u + a11*v + t1 (Eq. 1
+ * with basis vectors (a00,a10), (a01,a11) and origin (t0,t1)); otherwise the
+ * rect's pixel-centre map above. */
+void orc_crop(const uint8_t* grey, const uint16_t* depth, int H, int W,
+              const orc_rect* r, const int32_t* affine, int out_h, int out_w,
+              uint8_t* out_grey, uint16_t* out_depth) {
+    for (int v = 0; v < out_h; ++v) {
+        for (int u = 0; u < out_w; ++u) {
+            int64_t Xq, Yq;
+            if (affine) {
+                Xq = (int64_t)affine[0] * u + (int64_t)affine[1] * v + affine[2];
+                Yq = (int64_t)affine[3] * u + (int64_t)affine[4] * v + affine[5];
+            } else {
+                Xq = orc_rect_coord_q16(r->x, r->w, out_w, u);
+                Yq = orc_rect_coord_q16(r->y, r->h, out_h, v);
+            }
+            out_grey[v * out_w + u] = orc_bilinear_u8(grey, H, W, Xq, Yq);
+            out_depth[v * out_w + u] = orc_nearest_u16(depth, H, W, Xq, Yq);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* S2. Depth mask: the fusion region of interest (Sections 1 and 2.5). */
+/* ------------------------------------------------------------------ */
+
+static int cmp_u16(const void* a, const void* b) {
+    int x = *(const uint16_t*)a, y = *(const uint16_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* Lower median of the non-zero depth values: sort them and take index
+ * floor((n-1)/2).  Returns -1 when every value is a hole (zero). */
+int32_t orc_median_nonzero(const uint16_t* d, int n) {
+    uint16_t* buf = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)(n > 0 ? n : 1));
+    int m = 0;
+    for (int i = 0; i < n; ++i)
+        if (d[i] != 0) buf[m++] = d[i];
+    int32_t med = -1;
+    if (m > 0) {
+        qsort(buf, (size_t)m, sizeof(uint16_t), cmp_u16);
+        med = buf[(m - 1) / 2];
+    }
+    free(buf);
+    return med;
+}
+
+/* valid = (d != 0) and |d - median| < mask_mm (strict). */
+void orc_valid_mask(const uint16_t* d, int n, int32_t median, int mask_mm, uint8_t* valid) {
+    for (int i = 0; i < n; ++i) {
+        int32_t diff = (int32_t)d[i] - median;
+        if (diff < 0) diff = -diff;
+        valid[i] = (uint8_t)(median >= 0 && d[i] != 0 && diff < mask_mm);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* S3. LBP code, Eq. 2 read as sum_{p=0}^{7} s(g_p - g_c) 2^p.         */
+/* ------------------------------------------------------------------ */
+
+/* Neighbour p of the 3x3 ring, clockwise from top-left, y pointing down. */
+static const int RING_DX[8] = {-1, 0, 1, 1, 1, 0, -1, -1};
+static const int RING_DY[8] = {-1, -1, -1, 0, 1, 1, 1, 0};
+
+enum { ORC_LBP_GE = 1, ORC_LBP_NBR_IGNORE_MASK = 2 };
+
+/* Code of centre (i = row, j = column).  Neighbours outside the crop are
+ * replaced by the nearest crop pixel (replicate edge).  Bit p is set when the
+ * neighbour is depth-valid and brighter than the centre (strict, or >= with
+ * ORC_LBP_GE). */
+int orc_lbp_code(const uint8_t* g, const uint8_t* valid, int h, int w, int i, int j, int flags) {
+    int gc = g[i * w + j];
+    int code = 0;
+    for (int p = 0; p < 8; ++p) {
+        int r = i + RING_DY[p], c = j + RING_DX[p];
+        r = r < 0 ? 0 : (r > h - 1 ? h - 1 : r);
+        c = c < 0 ? 0 : (c > w - 1 ? w - 1 : c);
+        int gp = g[r * w + c];
+        int nbr_ok = (flags & ORC_LBP_NBR_IGNORE_MASK) ? 1 : valid[r * w + c];
+        int s = (flags & ORC_LBP_GE) ? (gp >= gc) : (gp > gc);
+        if (nbr_ok && s) code |= 1 << p;
+    }
+    return code;
+}
+
+/* ------------------------------------------------------------------ */
+/* S4. Histograms, Eq. 3, with the 59-bin uniform-pattern map.         */
+/* ------------------------------------------------------------------ */
+
+/* Number of 0/1 changes going once around the 8-bit ring. */
+static int ring_transitions(int c) {
+    int t = 0;
+    for (int p = 0; p < 8; ++p) {
+        int a = (c >> p) & 1;
+        int b = (c >> ((p + 1) % 8)) & 1;
+        t += (a != b);
+    }
+    return t;
+}
+
+/* lut[c] = rank of c among the codes with at most two transitions, in
+ * ascending code order (0..57); every other code maps to 58. */
+void orc_uniform_table(int32_t* lut) {
+    int rank = 0;
+    for (int c = 0; c < 256; ++c) {
+        if (ring_transitions(c) <= 2)
+            lut[c] = rank++;
+        else
+            lut[c] = -1;
+    }
+    for (int c = 0; c < 256; ++c)
+        if (lut[c] < 0) lut[c] = rank; /* rank == 58 here */
+}
+
+/* Per-cell histograms of one crop.  feat has (h/cell)*(w/cell)*nbins entries,
+ * cell-major row by row, bin fastest.  With nbins == 59 the uniform map is
+ * used; with nbins == 256 the raw code (the paper's 0-255 histogram). */
+void orc_histograms(const uint8_t* g, const uint8_t* valid, int h, int w, int cell,
+                    int nbins, int flags, uint16_t* feat) {
+    int32_t lut[256];
+    orc_uniform_table(lut);
+    int gx = w / cell, gy = h / cell;
+    memset(feat, 0, sizeof(uint16_t) * (size_t)gx * gy * nbins);
+    for (int i = 0; i < gy * cell; ++i) {
+        for (int j = 0; j < gx * cell; ++j) {
+            if (!valid[i * w + j]) continue;
+            int code = orc_lbp_code(g, valid, h, w, i, j, flags);
+            int bin = (nbins == 59) ? lut[code] : code;
+            int k = (i / cell) * gx + (j / cell);
+            feat[(size_t)k * nbins + bin] += 1;
+        }
+    }
+}
+
+/* Steps S1..S4 for a batch.  With rects == NULL the frames already are the
+ * crops (n_frames == n, H == out_h, W == out_w).  Invalid descriptors (frame
+ * out of range, non-positive side) give an all-zero feature row.  medians
+ * (nullable) receives the lower median per crop, -1 for an all-hole crop or
+ * an invalid descriptor. */
+void orc_features_batch(const uint8_t* grey, const uint16_t* depth, int n_frames, int H, int W,
+                        const orc_rect* rects, const int32_t* affine, int n, int out_h, int out_w,
+                        int cell, int mask_mm, int nbins, int flags, uint16_t* feats,
+                        int32_t* medians) {
+    size_t npx = (size_t)out_h * out_w;
+    size_t dim = (size_t)(out_h / cell) * (out_w / cell) * nbins;
+    uint8_t* cg = (uint8_t*)malloc(npx);
+    uint16_t* cd = (uint16_t*)malloc(npx * sizeof(uint16_t));
+    uint8_t* valid = (uint8_t*)malloc(npx);
+    for (int k = 0; k < n; ++k) {
+        uint16_t* out = feats + (size_t)k * dim;
+        if (rects) {
+            const orc_rect* r = &rects[k];
+            if (r->frame < 0 || r->frame >= n_frames || r->w <= 0 || r->h <= 0) {
+                memset(out, 0, dim * sizeof(uint16_t));
+                if (medians) medians[k] = -1;
+                continue;
+            }
+            orc_crop(grey + (size_t)r->frame * H * W, depth + (size_t)r->frame * H * W, H, W, r,
+                     affine ? affine + 6 * (size_t)k : NULL, out_h, out_w, cg, cd);
+        } else {
+            memcpy(cg, grey + (size_t)k * npx, npx);
+            memcpy(cd, depth + (size_t)k * npx, npx * sizeof(uint16_t));
+        }
+        int32_t med = orc_median_nonzero(cd, (int)npx);
+        if (medians) medians[k] = med;
+        orc_valid_mask(cd, (int)npx, med, mask_mm, valid);
+        orc_histograms(cg, valid, out_h, out_w, cell, nbins, flags, out);
+    }
+    free(cg);
+    free(cd);
+    free(valid);
+}
+
+/* ------------------------------------------------------------------ */
+/* S5. Per-cell normalisation and the SVM decision function (2.5).     */
+/* ------------------------------------------------------------------ */
+
+/* x_j = H_j / n_valid(cell), 0 for an empty cell.  fp64 form. */
+void orc_normalize_f64(const uint16_t* feats, int n, int cells, int nbins, double* x) {
+    for (int k = 0; k < n; ++k) {
+        for (int c = 0; c < cells; ++c) {
+            const uint16_t* h = feats + ((size_t)k * cells + c) * nbins;
+            double* o = x + ((size_t)k * cells + c) * nbins;
+            long tot = 0;
+            for (int b = 0; b < nbins; ++b) tot += h[b];
+            for (int b = 0; b < nbins; ++b) o[b] = tot ? (double)h[b] / (double)tot : 0.0;
+        }
+    }
+}
+
+/* The same quotient as one IEEE single-precision division. */
+void orc_normalize_f32(const uint16_t* feats, int n, int cells, int nbins, float* x) {
+    for (int k = 0; k < n; ++k) {
+        for (int c = 0; c < cells; ++c) {
+            const uint16_t* h = feats + ((size_t)k * cells + c) * nbins;
+            float* o = x + ((size_t)k * cells + c) * nbins;
+            long tot = 0;
+            for (int b = 0; b < nbins; ++b) tot += h[b];
+            for (int b = 0; b < nbins; ++b) {
+                volatile float num = (float)h[b], den = (float)tot;
+                o[b] = tot ? num / den : 0.0f;
+            }
+        }
+    }
+}
+
+/* fp32 -> bfloat16, round to nearest even (finite inputs). */
+uint16_t orc_f32_to_bf16(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+/* fp32 -> FP8 E4M3 (bias 7, max 448, no infinities), round to nearest even,
+ * saturating.  Finite inputs. */
+uint8_t orc_f32_to_e4m3(float f) {
+    double v = f;
+    uint8_t sign = 0;
+    if (v < 0) {
+        sign = 0x80;
+        v = -v;
+    }
+    if (v >= 448.0) return sign | 0x7E;
+    if (v == 0.0) return sign;
+    int e;
+    frexp(v, &e); /* v = m * 2^e, m in [0.5, 1): exponent of leading bit is e-1 */
+    int lead = e - 1;
+    if (lead < -6) lead = -6; /* subnormal range: quantum 2^-9 */
+    double quantum = ldexp(1.0, lead - 3);
+    double q = v / quantum; /* exact: power-of-two division */
+    double fl = floor(q);
+    double rem = q - fl;
+    double m = fl;
+    if (rem > 0.5 || (rem == 0.5 && fmod(fl, 2.0) != 0.0)) m = fl + 1.0;
+    int mi = (int)m;
+    int expf_field;
+    if (mi >= 16) { /* carried into the next binade */
+        mi = 8;
+        lead += 1;
+    }
+    if (mi < 8) { /* subnormal: exponent field 0 */
+        expf_field = 0;
+    } else {
+        expf_field = lead + 7;
+        mi -= 8;
+    }
+    int code = (expf_field << 3) | mi;
+    if (code > 0x7E) code = 0x7E;
+    return sign | (uint8_t)code;
+}
+
+double orc_e4m3_to_f64(uint8_t b) {
+    int s = b >> 7, e = (b >> 3) & 15, m = b & 7;
+    double v = (e == 0) ? ldexp((double)m, -9) : ldexp(1.0 + m / 8.0, e - 7);
+    return s ? -v : v;
+}
+
+/* RBF one-vs-rest decision: S[k][c] = sum_i a[c][i] exp(-gamma |x_k - sv_i|^2) + b[c],
+ * with |.|^2 summed term by term in fp64. */
+void orc_svm_rbf(const double* x, int n, const double* sv, int n_sv, int dim, const double* a,
+                 const double* b, int n_classes, double gamma, double* scores) {
+    double* kv = (double*)malloc(sizeof(double) * (size_t)(n_sv > 0 ? n_sv : 1));
+    for (int k = 0; k < n; ++k) {
+        const double* xk = x + (size_t)k * dim;
+        for (int i = 0; i < n_sv; ++i) {
+            const double* s = sv + (size_t)i * dim;
+            double d2 = 0.0;
+            for (int j = 0; j < dim; ++j) {
+                double t = xk[j] - s[j];
+                d2 += t * t;
+            }
+            kv[i] = exp(-gamma * d2);
+        }
+        for (int c = 0; c < n_classes; ++c) {
+            double acc = 0.0;
+            for (int i = 0; i < n_sv; ++i) acc += a[(size_t)c * n_sv + i] * kv[i];
+            scores[(size_t)k * n_classes + c] = acc + b[c];
+        }
+    }
+    free(kv);
+}
+
+/* Linear one-vs-rest decision: S[k][c] = w_c . x_k + b[c]. */
+void orc_svm_linear(const double* x, int n, int dim, const double* w, const double* b,
+                    int n_classes, double* scores) {
+    for (int k = 0; k < n; ++k) {
+        for (int c = 0; c < n_classes; ++c) {
+            double acc = 0.0;
+            for (int j = 0; j < dim; ++j) acc += w[(size_t)c * dim + j] * x[(size_t)k * dim + j];
+            scores[(size_t)k * n_classes + c] = acc + b[c];
+        }
+    }
+}
+
+/* Label = argmax over classes, lowest index on ties. */
+void orc_argmax(const double* scores, int n, int n_classes, int32_t* labels) {
+    for (int k = 0; k < n; ++k) {
+        int best = 0;
+        for (int c = 1; c < n_classes; ++c)
+            if (scores[(size_t)k * n_classes + c] > scores[(size_t)k * n_classes + best]) best = c;
+        labels[k] = best;
+    }
+}

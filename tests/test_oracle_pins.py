@@ -1,0 +1,338 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each value comes from a worked
+example in the paper (Fig. 7), a hand computation (tests/golden/), a closed
+form, an invariant, or an independent library routine (numpy sort, numpy IEEE
+float32 division, torch's bfloat16 / float8 casts, scikit-learn's SVM decision
+function).  Every function of oracle/rgbd_oracle.c is covered by at least one.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1504_01883_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rotl8(c, k):
+    return ((c << k) | (c >> (8 - k))) & 0xFF
+
+
+# ---------------------------------------------------------------------------------------------
+# S3: LBP codes (Eq. 2, Fig. 7)
+# ---------------------------------------------------------------------------------------------
+
+def test_fig7_worked_example(orc):
+    """Fig. 7: pattern 11110001 (bits 0,4,5,6,7 set, read from p7 down to p0) gives 241."""
+    # centre 50; p0, p4, p5, p6, p7 brighter; p1, p2, p3 darker.
+    #   p0 p1 p2      60 40 40
+    #   p7  c p3  ->  60 50 40
+    #   p6 p5 p4      60 60 60
+    g = np.array([[60, 40, 40], [60, 50, 40], [60, 60, 60]], np.uint8)
+    v = np.ones((3, 3), np.uint8)
+    assert orc.lbp_code(g, v, 1, 1) == 241
+    assert 241 == 0b11110001 == 1 + 16 + 32 + 64 + 128
+
+
+def _read_lbp_golden():
+    lines = [ln.split("#")[0].strip() for ln in open(os.path.join(GOLDEN, "lbp_4x4.txt"))]
+    lines = [ln for ln in lines if ln]
+    gi = lines.index("grey")
+    vi = lines.index("valid")
+    g = np.array([[int(t) for t in lines[gi + 1 + r].split()] for r in range(4)], np.uint8)
+    v = np.array([[int(t) for t in lines[vi + 1 + r].split()] for r in range(4)], np.uint8)
+    cases = [tuple(int(t) for t in ln.split()) for ln in lines[vi + 5:]]
+    return g, v, cases
+
+
+def test_lbp_hand_computed_4x4(orc):
+    g, v, cases = _read_lbp_golden()
+    assert len(cases) >= 10
+    for i, j, flags, code in cases:
+        assert orc.lbp_code(g, v, i, j, flags) == code, (i, j, flags)
+    # an invalid centre produces no code at all
+    codes = orc.lbp_codes(g, v)
+    assert codes[1, 2] == -1 and (codes >= 0).sum() == 15
+
+
+def test_constant_patch(orc):
+    g = np.full((16, 16), 77, np.uint8)
+    v = np.ones((16, 16), np.uint8)
+    assert (orc.lbp_codes(g, v) == 0).all()                 # strict > : no bit set
+    assert (orc.lbp_codes(g, v, orc.LBP_GE) == 255).all()   # >= would set all eight
+
+
+def test_rotation_bit_rotates_codes_and_permutes_cells(orc):
+    """Rotating grey and depth 90 degrees clockwise maps every code c to rotl8(c, 2)
+    and moves cell (cy, cx) to (cx, G-1-cy).  Holds only for a circular ring order."""
+    g, d = synth.crops(77, 1, 64)
+    g, d = g[0], d[0]
+    gr, dr = np.rot90(g, -1).copy(), np.rot90(d, -1).copy()
+    m = orc.median_nonzero(d)
+    assert orc.median_nonzero(dr) == m
+    v, vr = orc.valid_mask(d, m), orc.valid_mask(dr, m)
+    c, cr = orc.lbp_codes(g, v), orc.lbp_codes(gr, vr)
+    S = 64
+    ii, jj = np.nonzero(c >= 0)
+    assert ii.size > 1000
+    assert (cr[jj, S - 1 - ii] == _rotl8(c[ii, jj], 2)).all()
+    # histograms: cell permutation plus the bin permutation U(c) -> U(rotl8(c, 2))
+    lut = orc.uniform_table()
+    h = orc.histograms(g, v).reshape(8, 8, 59)
+    hr = orc.histograms(gr, vr).reshape(8, 8, 59)
+    perm = np.arange(59)
+    for code in range(256):
+        if lut[code] < 58:
+            perm[lut[code]] = lut[_rotl8(code, 2)]
+    for cy in range(8):
+        for cx in range(8):
+            moved = np.zeros(59, np.int64)
+            moved[perm] = h[cy, cx]
+            assert (hr[cx, 7 - cy] == moved).all()
+
+
+def test_cell_histogram_sums_to_valid_count(orc):
+    g, d = synth.crops(5, 1, 64)
+    m = orc.median_nonzero(d[0])
+    v = orc.valid_mask(d[0], m)
+    h = orc.histograms(g[0], v).reshape(8, 8, 59)
+    vc = v.reshape(8, 8, 8, 8).transpose(0, 2, 1, 3).sum(axis=(2, 3))
+    assert (h.sum(axis=2) == vc).all()
+    assert vc.sum() > 0.5 * 64 * 64  # face covers more than half of the crop
+    # the paper's own 0-255 histogram (Section 3) keeps the same count
+    h256 = orc.histograms(g[0], v, nbins=256).reshape(8, 8, 256)
+    assert (h256.sum(axis=2) == vc).all()
+
+
+def test_paper_range_histogram_bins_are_raw_codes(orc):
+    """Section 3's 0-255 histogram: one 3x3 cell, the Fig. 7 centre lands in bin 241."""
+    g = np.array([[60, 40, 40], [60, 50, 40], [60, 60, 60]], np.uint8)
+    v = np.ones((3, 3), np.uint8)
+    h = orc.histograms(g, v, cell=3, nbins=256)
+    assert h.shape == (256,) and h.sum() == 9 and h[241] >= 1
+
+
+# ---------------------------------------------------------------------------------------------
+# S4: the uniform-pattern map
+# ---------------------------------------------------------------------------------------------
+
+def test_uniform_table_closed_form(orc):
+    lut = orc.uniform_table()
+    P = 8
+    uniform = [c for c in range(256) if lut[c] < 58]
+    assert len(uniform) == P * (P - 1) + 2 == 58
+    # independent description: 0, 255 and every rotation of a run of k ones (k = 1..7)
+    runs = {0, 255}
+    for k in range(1, 8):
+        base = (1 << k) - 1
+        for r in range(8):
+            runs.add(_rotl8(base, r))
+    assert set(uniform) == runs
+    assert lut[0] == 0 and lut[255] == 57
+    assert list(lut[uniform]) == list(range(58))  # ranked in ascending code order
+    assert (lut[[c for c in range(256) if c not in runs]] == 58).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# S2: median and mask
+# ---------------------------------------------------------------------------------------------
+
+def test_median_matches_sort(orc):
+    rng = np.random.default_rng(3)
+    for n in [1, 2, 3, 4, 5, 64, 255, 4096]:
+        for hi in [3, 50, 65535]:
+            d = rng.integers(0, hi + 1, n).astype(np.uint16)
+            nz = np.sort(d[d != 0])
+            want = int(nz[(nz.size - 1) // 2]) if nz.size else -1
+            assert orc.median_nonzero(d) == want
+    assert orc.median_nonzero(np.zeros(10, np.uint16)) == -1
+    assert orc.median_nonzero(np.array([0, 9, 0], np.uint16)) == 9
+    assert orc.median_nonzero(np.array([4, 8], np.uint16)) == 4  # lower median
+
+
+def test_mask_strict_window(orc):
+    d = np.array([1000, 1149, 1150, 851, 850, 0, 65535], np.uint16)
+    assert list(orc.valid_mask(d, 1000, 150)) == [1, 1, 0, 1, 0, 0, 0]
+    assert list(orc.valid_mask(d, -1, 150)) == [0] * 7
+
+
+def test_all_hole_crop_gives_zero_features(orc):
+    g, _ = synth.crops(9, 1, 64)
+    d = np.zeros((1, 64, 64), np.uint16)
+    f, med = orc.features_batch(g, d, None, 64, return_medians=True)
+    assert med[0] == -1 and not f.any()
+
+
+def test_background_only_median(orc):
+    # a crop with no face: the mask keeps the depth band around the median
+    rng = np.random.default_rng(0)
+    d = rng.integers(2500, 4001, (64, 64)).astype(np.uint16)
+    m = orc.median_nonzero(d)
+    v = orc.valid_mask(d, m)
+    assert v.sum() == ((np.abs(d.astype(int) - m) < 150)).sum()
+
+
+# ---------------------------------------------------------------------------------------------
+# S1: resample
+# ---------------------------------------------------------------------------------------------
+
+def _read_resample_golden():
+    cases = []
+    lines = [ln.split("#")[0].strip() for ln in open(os.path.join(GOLDEN, "resample_small.txt"))]
+    lines = [ln for ln in lines if ln]
+    i = 0
+    while i < len(lines):
+        t = lines[i].split()
+        assert t[0] == "case"
+        H, W, x, y, w, h, oh, ow = map(int, t[2:])
+        i += 1
+        blocks = {}
+        for name, rows in [("grey_in", H), ("depth_in", H), ("grey_out", oh), ("depth_out", oh)]:
+            assert lines[i] == name
+            blocks[name] = np.array([[int(v) for v in lines[i + 1 + r].split()] for r in range(rows)])
+            i += 1 + rows
+        cases.append(((x, y, w, h), oh, ow, blocks))
+    return cases
+
+
+def test_resample_hand_computed(orc):
+    cases = _read_resample_golden()
+    assert len(cases) == 3
+    for rect, oh, ow, b in cases:
+        og, od = orc.crop(b["grey_in"].astype(np.uint8), b["depth_in"].astype(np.uint16), rect, oh, ow)
+        assert (og == b["grey_out"]).all(), rect
+        assert (od == b["depth_out"]).all(), rect
+
+
+def test_resample_identity_and_translation(orc):
+    g, d = synth.crops(11, 1, 64)
+    og, od = orc.crop(g[0], d[0], (0, 0, 64, 64), 64, 64)
+    assert (og == g[0]).all() and (od == d[0]).all()
+    assert orc.rect_coord_q16(0, 64, 64, 5) == 5 * 65536
+    # integer translation through the general affine form (Eq. 1 with unit basis vectors)
+    aff = np.array([65536, 0, 7 * 65536, 0, 65536, 3 * 65536], np.int32)
+    big_g = np.pad(g[0], 16, mode="edge")
+    big_d = np.pad(d[0], 16, mode="edge")
+    ag, ad = orc.crop(big_g, big_d, (0, 0, 1, 1), 32, 32, affine=aff)
+    assert (ag == big_g[3:35, 7:39]).all() and (ad == big_d[3:35, 7:39]).all()
+
+
+def test_resample_constant_image_is_exact(orc):
+    # the Q8 weights sum to 2^16, so any rect over a constant image returns the constant
+    g = np.full((40, 50), 173, np.uint8)
+    d = np.full((40, 50), 1234, np.uint16)
+    for rect in [(3, 4, 17, 29), (-10, -10, 90, 70), (45, 35, 30, 30)]:
+        og, od = orc.crop(g, d, rect, 13, 11)
+        assert (og == 173).all() and (od == 1234).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# S5: normalisation, quantisation and the SVM decision function
+# ---------------------------------------------------------------------------------------------
+
+def test_normalize_matches_ieee_division(orc):
+    rng = np.random.default_rng(1)
+    f = rng.integers(0, 5, (3, 4 * 59)).astype(np.uint16)
+    f[0, :59] = 0  # an empty cell
+    x32 = orc.normalize_f32(f)
+    tot = f.reshape(3, 4, 59).sum(axis=2, keepdims=True).astype(np.float32)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        want = np.where(tot > 0, f.reshape(3, 4, 59).astype(np.float32) / tot, 0).astype(np.float32)
+    assert (x32.reshape(3, 4, 59).view(np.uint32) == want.view(np.uint32)).all()
+    x64 = orc.normalize_f64(f).reshape(3, 4, 59)
+    s = x64.sum(axis=2)
+    assert np.allclose(s[tot[..., 0] > 0], 1.0) and (s[tot[..., 0] == 0] == 0).all()
+    # every quotient h / n of two counts n <= 64 rounds as numpy's IEEE float32 division
+    for n in range(1, 65):
+        for hv in range(0, n + 1):
+            row = np.zeros((1, 59), np.uint16)
+            row[0, 0], row[0, 1] = hv, n - hv
+            got = orc.normalize_f32(row)[0, 0]
+            assert got.view(np.uint32) == (np.float32(hv) / np.float32(n)).view(np.uint32)
+
+
+def test_bf16_and_e4m3_match_torch():
+    torch = pytest.importorskip("torch")
+    import oracle
+    rng = np.random.default_rng(2)
+    x = np.concatenate([rng.random(2000).astype(np.float32),
+                        rng.random(500).astype(np.float32) * 448.0,
+                        np.array([0.0, 1.0 / 64, 1.0 / 59, 2.0 ** -9, 2.0 ** -10, 447.9, 448.0],
+                                 np.float32)])
+    bf = oracle.f32_to_bf16(x)
+    tb = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert (bf == tb).all()
+    if hasattr(torch, "float8_e4m3fn"):
+        e = oracle.f32_to_e4m3(x)
+        te = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+        assert (e == te).all()
+        back = oracle.e4m3_to_f64(e)
+        tb2 = torch.from_numpy(te).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+        assert (back == tb2).all()
+
+
+def test_rbf_matches_sklearn_decision_function(orc):
+    sklearn = pytest.importorskip("sklearn")
+    from sklearn.svm import SVC
+    rng = np.random.default_rng(4)
+    X = rng.random((60, 12))
+    y = (X[:, 0] + 0.3 * X[:, 3] > 0.7).astype(int)
+    gamma = 1.0 / 12
+    clf = SVC(kernel="rbf", gamma=gamma, C=3.0).fit(X, y)
+    Xt = rng.random((25, 12))
+    s = orc.svm_rbf(Xt, clf.support_vectors_, clf.dual_coef_, clf.intercept_, gamma)
+    assert np.allclose(s[:, 0], clf.decision_function(Xt), rtol=1e-12, atol=1e-12)
+
+
+def test_linear_matches_sklearn_and_identity(orc):
+    pytest.importorskip("sklearn")
+    from sklearn.svm import LinearSVC
+    rng = np.random.default_rng(5)
+    X = rng.random((80, 9))
+    y = rng.integers(0, 3, 80)
+    clf = LinearSVC(C=1.0, max_iter=20000).fit(X, y)
+    Xt = rng.random((10, 9))
+    s = orc.svm_linear(Xt, clf.coef_, clf.intercept_)
+    assert np.allclose(s, clf.decision_function(Xt), rtol=1e-12, atol=1e-12)
+    # W = I, b: the score is x + b
+    b = np.array([0.5, -1.0, 2.0])
+    x = rng.random((4, 3))
+    assert np.allclose(orc.svm_linear(x, np.eye(3), b), x + b, rtol=0, atol=1e-15)
+
+
+def test_rbf_special_cases(orc):
+    x = np.array([[0.25, 0.5, 0.125]])
+    # one support vector equal to x: K = 1 exactly
+    s = orc.svm_rbf(x, x.copy(), np.array([[2.5]]), np.array([-1.0]), 0.7)
+    assert s[0, 0] == 1.5
+    # far support vector: K underflows to 0, score = bias
+    s = orc.svm_rbf(x, x + 1e3, np.array([[2.5]]), np.array([-1.0]), 0.7)
+    assert s[0, 0] == -1.0
+
+
+def test_argmax_lowest_index_on_ties(orc):
+    s = np.array([[1.0, 3.0, 3.0], [2.0, 2.0, 2.0], [-1.0, -5.0, 0.0]])
+    assert list(orc.argmax(s)) == [1, 0, 2]
+
+
+# ---------------------------------------------------------------------------------------------
+# Composition of S1..S4 on a frame
+# ---------------------------------------------------------------------------------------------
+
+def test_features_batch_composes_steps(orc):
+    g, d, r = synth.frames_with_rects(21, 1, 3, 40, 90, H=120, W=160)
+    feats, meds = orc.features_batch(g, d, r, out_h=64, return_medians=True)
+    for k in range(3):
+        rr = r[k]
+        cg, cd = orc.crop(g[0], d[0], (rr["x"], rr["y"], rr["w"], rr["h"]), 64, 64)
+        m = orc.median_nonzero(cd)
+        assert m == meds[k]
+        v = orc.valid_mask(cd, m)
+        assert (orc.histograms(cg, v) == feats[k]).all()
+    # an invalid descriptor gives a zero row
+    bad = r.copy()
+    bad[1]["frame"] = 5
+    f2 = orc.features_batch(g, d, bad, out_h=64)
+    assert not f2[1].any() and (f2[0] == feats[0]).all()
