@@ -1,0 +1,365 @@
+"""Benchmark of the depth-fused LBP + SVM hot path (one GB300).
+
+A step is one pass of the whole path over one batch: for every face rect of 256 synthetic
+640x480 RGB-D frames (4096 rects, sides U{48..256}), the fused kernel crops it to 128x128,
+masks it around its median depth, computes the LBP codes and the 16x16 cells' 59-bin
+histograms (15104-dim uint16 rows) and the per-cell normalised rows; then the RBF SVM
+(4096 support vectors, 64 classes, gamma = 1/dim) scores every row and takes the argmax.
+
+    python bench.py [--steps K] [--warmup W] [--score-dtype tf32|bf16|fp8|f32]
+    python bench.py --impl reference     # the CPU oracle on a bounded sample, same metric
+
+Prints one JSON line (see the keys below).  Inputs are resident in HBM for `value`; `e2e`
+repeats the step through the same C-ABI calls from pinned host buffers, with the frame
+upload and the score / label read-back inside the timed region.  Between timed steps a
+256 MB buffer is written to flush the 129 MB L2.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# nominal dense tensor rates relative to bf16 (2.25 PF): fp8 4.5, tf32 1.1
+NOMINAL_RATIO = {"bf16": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25}
+DT_CODE = {"f32": 1, "bf16": 2, "fp8": 3, "tf32": 4}
+X_ELEM = {"f32": 4, "tf32": 4, "bf16": 2, "fp8": 1}
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return dict(FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes_k1(rects, H, W, crop, x_elem, k_pad, dim):
+    """Bytes the fused kernel must move per launch: the source pixels of each rect inside the
+    frame (grey 1 B; depth 2 B, at most crop^2 of them since depth is sampled, not filtered)
+    plus its outputs (uint16 row, normalised row, squared norm)."""
+    x0 = np.clip(rects["x"], 0, W)
+    x1 = np.clip(rects["x"] + rects["w"], 0, W)
+    y0 = np.clip(rects["y"], 0, H)
+    y1 = np.clip(rects["y"] + rects["h"], 0, H)
+    area = (x1 - x0).astype(np.int64) * (y1 - y0).astype(np.int64)
+    grey = area.sum()
+    depth = 2 * np.minimum(area, crop * crop).sum()
+    out = len(rects) * (2 * dim + x_elem * k_pad + 4)
+    return int(grey + depth + out)
+
+
+def cpu_baseline(wl, n_sample=48, time_budget_s=25.0):
+    """The oracle, as it stands, on a bounded sample of the workload: the first faces' features
+    and their fp64 RBF scores against every support vector.  Returns crops/s and the sample."""
+    import oracle as orc
+    t0 = time.perf_counter()
+    sv64 = orc.normalize_f64(wl.sv_counts)
+    t_sv = time.perf_counter() - t0
+    done = 0
+    t_start = time.perf_counter()
+    for k in range(n_sample):
+        r = wl.rects[k:k + 1]
+        f = orc.features_batch(wl.grey, wl.depth, r, wl.crop)
+        x = orc.normalize_f64(f)
+        orc.svm_rbf(x, sv64, wl.coef, wl.bias, wl.gamma)
+        done += 1
+        if time.perf_counter() - t_start > time_budget_s:
+            break
+    el = time.perf_counter() - t_start
+    return {"value": done / el, "unit": "crops/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} of {wl.n_crops} faces: crop+mask+LBP+histograms and fp64 RBF scores "
+                      f"against all {wl.sv_counts.shape[0]} SVs, single thread ({el:.1f} s; SV normalisation "
+                      f"{t_sv:.1f} s excluded)"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle (the only reference implementation there is)."""
+    from paper_1504_01883_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    wl = synth.batching()
+    per_step = max(1, args.ref_crops_per_step)
+    vals = []
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(wl, per_step, 1e9)
+        if s >= args.warmup:
+            vals.append(cb["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "crops/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * per_step / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl, "f64"),
+            "cpu_baseline": {"value": v, "unit": "crops/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} faces per step of the 4096-face batch, single thread"},
+            "e2e": {"value": v, "unit": "crops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+METRIC = "fused RGB-D LBP+SVM crops/s"
+
+
+def workload_config(wl, score_dtype):
+    return {"workload": "batch: 256 frames 640x480 (uint8 grey + uint16 depth), 4096 face rects of side "
+                        "U{48..256} -> 128x128 crops, 16x16 cells x 59 bins (15104-dim), RBF SVM 4096 SV x 64 "
+                        "classes, gamma=1/15104",
+            "n_crops": int(wl.n_crops), "n_sv": int(wl.sv_counts.shape[0]), "n_classes": int(wl.coef.shape[0]),
+            "crop": wl.crop, "dim": wl.dim, "score_dtype": score_dtype,
+            "l2": "flushed between timed steps (256 MB write)", "graph": "CUDA graph per stage"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--score-dtype", default="tf32", choices=["tf32", "bf16", "fp8", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-crops-per-step", type=int, default=8)
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1504_01883_gb300 import _build
+    from paper_1504_01883_gb300 import binding as B
+    from paper_1504_01883_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+
+    dt = args.score_dtype
+    wl = synth.batching(seed=1506 + rank)  # replicas: each rank its own batch (weak scaling)
+    n, dim, crop = wl.n_crops, wl.dim, wl.crop
+    k_pad = B.k_pad_for(dim)
+    dev = torch.device("cuda", local)
+    ctx = B.Context(local)
+
+    grey = torch.from_numpy(wl.grey).to(dev)
+    depth = torch.from_numpy(wl.depth.view(np.int16)).to(dev)
+    rects = B.rects_tensor(wl.rects, dev)
+    sv = torch.from_numpy(wl.sv_counts.view(np.int16)).to(dev)
+    model = B.svm_train_data_pack(ctx, sv, torch.from_numpy(wl.coef).to(dev), torch.from_numpy(wl.bias).to(dev),
+                                  gamma=wl.gamma, dtype=dt)
+    x_scale = 448.0
+    feats = torch.empty((n, dim), dtype=torch.int16, device=dev)
+    x = torch.empty((n, k_pad), dtype=B.x_torch_dtype(DT_CODE[dt]), device=dev)
+    xsq = torch.empty((n,), dtype=torch.float32, device=dev)
+    scores = torch.empty((n, wl.coef.shape[0]), dtype=torch.float32, device=dev)
+    labels = torch.empty((n,), dtype=torch.int32, device=dev)
+    out = {"feats": feats, "x": x, "xsq": xsq}
+
+    stream = torch.cuda.Stream(device=dev)
+
+    def stage1():
+        B.lbp_fused_features(ctx, grey, depth, rects, crop=crop, x_dtype=DT_CODE[dt], x_scale=x_scale, out=out,
+                             stream=stream)
+
+    def stage2():
+        B.svm_score(ctx, model, x, xsq, x_scale=x_scale, scores=scores, labels=labels, stream=stream)
+
+    with torch.cuda.stream(stream):
+        stage1()
+        stage2()
+    torch.cuda.synchronize()
+    ctx.status(clear=True)
+
+    g1, g2 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g1, stream=stream):
+        stage1()
+    with torch.cuda.graph(g2, stream=stream):
+        stage2()
+    launches_per_step = 4 if dt != "f32" else 3  # K1; [asum_split,] scoring, reduce
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+
+    for _ in range(max(3, args.warmup)):
+        flush_l2()
+        g1.replay()
+        g2.replay()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush_l2()
+        with torch.cuda.stream(stream):
+            ev[i][0].record(stream)
+            g1.replay()
+            ev[i][1].record(stream)
+            g2.replay()
+            ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_step = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    t_k1 = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    t_k2 = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    total_ms = float(np.sum(t_step))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms / 1000.0)
+    status = ctx.status(clear=True)
+
+    # ---- end to end through the same calls, from pinned host memory --------------------------
+    h_grey = torch.from_numpy(wl.grey).pin_memory()
+    h_depth = torch.from_numpy(wl.depth.view(np.int16)).pin_memory()
+    h_rects = B.rects_tensor(wl.rects, "cpu").pin_memory()
+    h_scores = torch.empty_like(scores, device="cpu").pin_memory()
+    h_labels = torch.empty_like(labels, device="cpu").pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for it in range(e2e_steps + 2):
+        if it == 2:
+            evs[0].record(stream)
+        with torch.cuda.stream(stream):
+            grey.copy_(h_grey, non_blocking=True)
+            depth.copy_(h_depth, non_blocking=True)
+            rects.copy_(h_rects, non_blocking=True)
+            stage1()
+            stage2()
+            h_scores.copy_(scores, non_blocking=True)
+            h_labels.copy_(labels, non_blocking=True)
+    evs[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = evs[0].elapsed_time(evs[1]) / e2e_steps
+    h2d = h_grey.numel() + 2 * h_depth.numel() + 4 * h_rects.numel()
+    d2h = 4 * h_scores.numel() + 4 * h_labels.numel()
+
+    # ---- roofline of the dominant kernel --------------------------------------------------
+    pk, src = peaks()
+    k1_ms, k2_ms = float(np.mean(t_k1)), float(np.mean(t_k2))
+    k1_bytes = algorithmic_bytes_k1(wl.rects, 480, 640, crop, X_ELEM[dt], k_pad, dim)
+    k1_gbs = k1_bytes / (k1_ms * 1e-3) / 1e9
+    n_sv = wl.sv_counts.shape[0]
+    C = wl.coef.shape[0]
+    k2_flops = 2.0 * n * n_sv * dim + 2.0 * n * n_sv * C
+    k2_tflops = k2_flops / (k2_ms * 1e-3) / 1e12
+    if dt == "f32":
+        peak_t = None
+    else:
+        peak_t = pk["bf16_tflops"] * NOMINAL_RATIO[dt]
+    rl_k1 = {"kernel": "lbp_fused_kernel<128>", "bound": "hbm", "achieved": round(k1_gbs, 1),
+             "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(k1_gbs / pk["hbm_gbs"], 4),
+             "traffic": None, "algorithmic_bytes": k1_bytes, "ms": round(k1_ms, 4), "peak_source": src}
+    rl_k2 = {"kernel": "rbf_tc_kernel" if dt != "f32" else "rbf_tiled_kernel", "bound": "tensor" if peak_t else "alu",
+             "achieved": round(k2_tflops, 1), "peak": round(peak_t, 1) if peak_t else None, "unit": "TFLOP/s",
+             "frac": round(k2_tflops / peak_t, 4) if peak_t else None, "traffic": None,
+             "algorithmic_flops": k2_flops, "ms": round(k2_ms, 4), "peak_source": src}
+    dominant = rl_k2 if k2_ms >= k1_ms else rl_k1
+    roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roofline["kernel"] = dominant["kernel"]
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "crops/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": f"u8/u16 integer LBP; {dt} scoring",
+            "data": "synthetic", "config": workload_config(wl, dt),
+            "roofline": roofline, "stages": {"k1": rl_k1, "k2": rl_k2},
+            "e2e": {"value": round(world * n / (e2e_ms * 1e-3), 1), "unit": "crops/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk, "device_status": status}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(line))
+    model.free()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

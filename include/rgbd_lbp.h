@@ -1,0 +1,230 @@
+/*
+ * rgbd_lbp.h -- C ABI of the GB300 (sm_103a) depth-fused LBP + SVM library.
+ *
+ * The library implements the GPU hot path of Naik & Rathna, "Robust real time
+ * face recognition and tracking on GPU using fusion of RGB and depth image"
+ * (arXiv 1504.01883): for each face rectangle, an affine resample of the grey
+ * and depth frames (Section 2.1, Eq. 1), a depth mask around the face's median
+ * depth (the depth/grey fusion of Sections 1 and 2.5), 8-neighbour radius-1 LBP
+ * codes (Section 2.4, Eq. 2, Fig. 7), per-cell uniform-pattern histograms
+ * concatenated into the feature vector (Section 2.4, Eq. 3; Section 3), and
+ * the SVM decision function that scores those vectors (Section 2.5).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int status: RGBD_OK (0) or a negative RGBD_ERR_*.
+ *    rgbd_last_error() returns the calling thread's last message.  Nothing
+ *    throws across this boundary.
+ *  - Every data pointer is a DEVICE pointer owned by the caller, unless the
+ *    argument says otherwise.  The library owns only rgbd_ctx and rgbd_svm.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued asynchronously on it; only argument checks
+ *    run synchronously.  A call that must grow the context workspace
+ *    allocates device memory first (synchronous); call rgbd_ctx_reserve()
+ *    before capturing calls into a CUDA graph.
+ *  - Sizes are int32 element counts; arrays are dense and row-major.
+ *  - Problems that only the device can see (a descriptor whose frame index is
+ *    out of range, a pipeline wait that ran out of time) do not abort the
+ *    call: the affected output rows are written as zeros and a bit is set in
+ *    the context's status word, read with rgbd_ctx_status().
+ */
+#ifndef RGBD_LBP_H
+#define RGBD_LBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------------------- */
+#define RGBD_OK 0
+#define RGBD_ERR_ARG (-1)         /* an argument is out of range or inconsistent */
+#define RGBD_ERR_NOMEM (-2)       /* device allocation failed */
+#define RGBD_ERR_CUDA (-3)        /* a CUDA runtime call or a launch failed */
+#define RGBD_ERR_TIMEOUT (-4)     /* a device-side wait ran out of time */
+#define RGBD_ERR_UNSUPPORTED (-5) /* a valid request this build does not implement */
+
+/* ---- bits of the device status word (rgbd_ctx_status) ------------------------------- */
+#define RGBD_STATUS_BAD_RECT 0x1u     /* a descriptor had frame out of range or w, h <= 0 */
+#define RGBD_STATUS_WAIT_TIMEOUT 0x2u /* a bounded pipeline wait expired; outputs are invalid */
+
+/* ---- element types of normalised feature rows and packed models ---------------------- */
+#define RGBD_DT_F32 1  /* fp32 storage, scored with exact fp32 SIMT arithmetic */
+#define RGBD_DT_BF16 2 /* bfloat16 storage, scored on tcgen05 tensor cores, fp32 accumulate */
+#define RGBD_DT_FP8 3  /* FP8 E4M3 storage with a per-tensor scale, tcgen05, fp32 accumulate */
+#define RGBD_DT_TF32 4 /* fp32 storage, scored on tcgen05 tensor cores as TF32 */
+
+/* ---- SVM kernels ------------------------------------------------------------------------- */
+#define RGBD_KERNEL_LINEAR 0 /* S_c = w_c . x + b_c */
+#define RGBD_KERNEL_RBF 1    /* S_c = sum_i a_ci exp(-gamma |x - sv_i|^2) + b_c */
+
+/* ---- LBP option flags ------------------------------------------------------------------- */
+#define RGBD_LBP_GE 0x1               /* s(g_p - g_c) = [g_p >= g_c] instead of [g_p > g_c] */
+#define RGBD_LBP_NBR_IGNORE_MASK 0x2  /* neighbours compare on grey whatever their depth */
+
+/* A face rectangle on frame `frame`: top-left (x, y), width w, height h, in
+ * frame pixels.  It may extend past the frame border (taps are clamped). */
+typedef struct rgbd_rect {
+    int32_t frame, x, y, w, h;
+} rgbd_rect;
+
+typedef struct rgbd_ctx rgbd_ctx;
+typedef struct rgbd_svm rgbd_svm;
+
+/* Shape of a packed model (host struct filled by rgbd_svm_get_info). */
+typedef struct rgbd_svm_info {
+    int32_t kernel;    /* RGBD_KERNEL_* */
+    int32_t dtype;     /* RGBD_DT_* of the packed support vectors */
+    int32_t n_sv;      /* support vectors (0 for a linear model) */
+    int32_t n_sv_pad;  /* rows of the packed SV matrix */
+    int32_t dim;       /* feature length (cells * nbins) */
+    int32_t k_pad;     /* row stride of packed vectors and of x given to svm_score */
+    int32_t n_classes;
+    int32_t scorable;  /* 0 when packed without coefficients */
+    float gamma;
+    float sv_scale;    /* FP8 per-tensor scale of the SVs (1 otherwise) */
+} rgbd_svm_info;
+
+/* ======================================================================================= */
+/* Context                                                                                 */
+/* ======================================================================================= */
+
+/* Library version, (major << 16) | minor. */
+int rgbd_version(void);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated to
+ * len) into buf.  Returns the untruncated length.  buf: host memory. */
+int rgbd_last_error(char* buf, size_t len);
+
+/* Creates a context bound to CUDA device `device`: a device status word, the
+ * workspace (grown on demand) and cached device properties.  *out receives a
+ * library-owned handle, freed by rgbd_ctx_destroy.  Errors: RGBD_ERR_ARG (bad
+ * device, out == NULL), RGBD_ERR_CUDA, RGBD_ERR_NOMEM. */
+int rgbd_ctx_create(int device, rgbd_ctx** out);
+
+/* Frees the context and its device memory.  Synchronises the device first. */
+int rgbd_ctx_destroy(rgbd_ctx* ctx);
+
+/* Grows the context workspace to at least `bytes` (synchronous).  Call it
+ * before capturing library calls into a CUDA graph. */
+int rgbd_ctx_reserve(rgbd_ctx* ctx, size_t bytes);
+
+/* Reads the device status word (synchronises the device).  flags (host) may be
+ * NULL; with clear != 0 the word is reset to 0 afterwards. */
+int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear);
+
+/* ======================================================================================= */
+/* A1: affine crop (Section 2.1, Eq. 1 p' = x.u + y.v + t; Section 3: each face is      */
+/* resized to a fixed square)                                                              */
+/* ======================================================================================= */
+
+/* Resamples n_rects rectangles of the registered grey / depth frames into
+ * out_h x out_w crops.
+ *   grey   uint8  [n_frames][H][W]
+ *   depth  uint16 [n_frames][H][W], millimetres, 0 = hole
+ *   rects  rgbd_rect [n_rects] (device)
+ *   affine_q16  NULL, or int32 [n_rects][6] = (a00, a01, t0, a10, a11, t1) in
+ *          Q16.16: crop pixel (u, v) reads source point
+ *          (a00*u + a01*v + t0, a10*u + a11*v + t1) / 2^16 (Eq. 1 with basis
+ *          vectors (a00, a10), (a01, a11) and origin (t0, t1)).  When NULL the
+ *          rect maps pixel centres to pixel centres:
+ *          X_q(u) = x*2^16 + floor((2u+1) * w * 2^16 / (2*out_w)) - 2^15.
+ *   out_grey  uint8  [n_rects][out_h][out_w]: bilinear, Q8 weights, round half up
+ *   out_depth uint16 [n_rects][out_h][out_w]: nearest, never interpolated
+ * Taps outside the frame are clamped to the border.  A descriptor with frame
+ * out of range or w, h <= 0 gives zero crops and RGBD_STATUS_BAD_RECT.
+ * Errors: RGBD_ERR_ARG (NULL pointers, n_rects < 0, sizes <= 0). */
+int rgbd_crop_affine(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, int n_frames, int H,
+                     int W, const rgbd_rect* rects, const int32_t* affine_q16, int n_rects,
+                     int out_h, int out_w, uint8_t* out_grey, uint16_t* out_depth, void* stream);
+
+/* ======================================================================================= */
+/* A1-A5 fused: crop, median-depth mask, LBP codes, uniform-59 cell histograms and      */
+/* the per-cell normalisation, in one persistent launch (Sections 2.1, 2.4, 3)            */
+/* ======================================================================================= */
+
+/* For each of n faces: the crop of A1 (crop x crop), the lower median m of the
+ * crop's non-zero depths, the mask valid = (d != 0 && |d - m| < mask_mm), the
+ * LBP code of every valid centre (ring p0..p7 clockwise from the top-left
+ * neighbour, bit p set when neighbour p is valid and brighter; neighbours past
+ * the crop edge replicate it), and one 59-bin histogram per cell x cell block
+ * (bins: the 58 codes with at most two circular 0/1 transitions in ascending
+ * code order, then one bin for all others).
+ *   rects == NULL: the frames already are the crops (n_frames == n,
+ *          H == W == crop) and affine_q16 must be NULL.
+ *   crop   32, 64, 96 or 128; cell must be 8; mask_mm > 0.
+ *   flags  RGBD_LBP_* bits.
+ *   feats  uint16 [n][dim], dim = (crop/8)^2 * 59, cell-major, bin fastest;
+ *          may be NULL when x_out is given.
+ *   x_dtype / x_out / k_pad / x_scale: optional normalised rows
+ *          x_j = H_j / n_valid(cell) (IEEE fp32 quotient, 0 for an empty cell),
+ *          stored as RGBD_DT_F32 / RGBD_DT_TF32 (float), RGBD_DT_BF16 (round
+ *          to nearest even) or RGBD_DT_FP8 (E4M3 of x * x_scale, round to
+ *          nearest even, saturating); row stride k_pad >= dim, a multiple of
+ *          128; columns dim..k_pad-1 are written as 0.  x_dtype 0 = none.
+ *   xsq_out  NULL or float [n]: sum of squares of the values x_out represents
+ *          (for FP8, of the decoded code / x_scale).
+ * Errors: RGBD_ERR_ARG, RGBD_ERR_UNSUPPORTED (cell != 8, crop outside the
+ * range), RGBD_ERR_CUDA. */
+int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, int n_frames,
+                       int H, int W, const rgbd_rect* rects, const int32_t* affine_q16, int n,
+                       int crop, int cell, int mask_mm, int flags, uint16_t* feats, int x_dtype,
+                       void* x_out, int k_pad, float x_scale, float* xsq_out, void* stream);
+
+/* A5 alone: per-cell normalisation of count rows that came from elsewhere (a
+ * stored database, synthetic counts).  feats uint16 [n][dim], dim a multiple
+ * of nbins; other arguments as in lbp_fused_features. */
+int lbp_normalize_features(rgbd_ctx* ctx, const uint16_t* feats, int n, int dim, int nbins,
+                           int x_dtype, void* x_out, int k_pad, float x_scale, float* xsq_out,
+                           void* stream);
+
+/* ======================================================================================= */
+/* A5-A7: the SVM (Section 2.5: one-vs-rest, "faces" vs "non-faces" per person)           */
+/* ======================================================================================= */
+
+/* Packs a trained SVM into a device-resident model (synchronous on `stream`).
+ *   RBF:    sv_feats uint16 [n_sv][dim] are the support vectors' count rows
+ *           (normalised per cell here); coef float [n_classes][n_sv] holds
+ *           a_ci = alpha_ci * y_ci; gamma > 0.
+ *   LINEAR: sv_feats NULL, n_sv 0; coef float [n_classes][dim] holds w_c.
+ *   bias   float [n_classes] (NULL = zeros).
+ *   dtype  RGBD_DT_*: how SVs are stored and scored (FP8: per-tensor scale
+ *          448 / max|sv|, reported in rgbd_svm_info.sv_scale).  A linear
+ *          model is always RGBD_DT_F32.
+ *   coef == NULL packs only the normalised SV matrix (for a host trainer,
+ *          Section 3 trains on the CPU); such a model is not scorable.
+ * *model_out receives a library-owned handle (free with rgbd_svm_free).
+ * Errors: RGBD_ERR_ARG, RGBD_ERR_NOMEM, RGBD_ERR_CUDA. */
+int svm_train_data_pack(rgbd_ctx* ctx, const uint16_t* sv_feats, int n_sv, int dim, int nbins,
+                        const float* coef, const float* bias, int n_classes, int kernel,
+                        float gamma, int dtype, rgbd_svm** model_out, void* stream);
+
+int rgbd_svm_free(rgbd_svm* model);
+
+/* info: host struct. */
+int rgbd_svm_get_info(const rgbd_svm* model, rgbd_svm_info* info);
+
+/* Device pointers of the packed SV matrix ([n_sv_pad][k_pad], model dtype) and
+ * of the squared norms of its rows (float [n_sv_pad]); either may be NULL. */
+int rgbd_svm_packed_sv(const rgbd_svm* model, const void** sv, const float** sv_sq);
+
+/* Scores n normalised rows.
+ *   x       [n][k_pad] in the model's dtype (float for F32 / TF32 / linear),
+ *           as written by lbp_fused_features or lbp_normalize_features.
+ *   xsq     float [n], squared norms of the rows (RBF only; may be NULL for a
+ *           linear model).
+ *   x_scale FP8 per-tensor scale of x (ignored for other dtypes).
+ *   scores  float [n][n_classes]: S_c = sum_i a_ci exp(-gamma |x - sv_i|^2) + b_c
+ *           (RBF) or w_c . x + b_c (linear).
+ *   labels  NULL or int32 [n]: argmax_c S_c, lowest index on ties.
+ * Uses context workspace (partial sums), grown on demand.
+ * Errors: RGBD_ERR_ARG, RGBD_ERR_UNSUPPORTED, RGBD_ERR_NOMEM, RGBD_ERR_CUDA. */
+int svm_score(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* xsq, int n,
+              float x_scale, float* scores, int32_t* labels, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RGBD_LBP_H */

@@ -1,0 +1,272 @@
+"""Thin Python binding of ``librgbdlbp.so`` (argument marshalling only).
+
+Every function here has the name of a C entry point in ``include/rgbd_lbp.h``
+and does nothing but check tensor shapes / dtypes, allocate outputs with torch
+(device memory is torch's), and pass raw pointers plus torch's current CUDA
+stream to the library.  All arithmetic of the method runs in the library's
+kernels.  If the library has not been built, ``lib()`` raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librgbdlbp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rgbd_lbp.h")
+
+RGBD_OK = 0
+DT_F32, DT_BF16, DT_FP8, DT_TF32 = 1, 2, 3, 4
+KERNEL_LINEAR, KERNEL_RBF = 0, 1
+LBP_GE, LBP_NBR_IGNORE_MASK = 1, 2
+STATUS_BAD_RECT, STATUS_WAIT_TIMEOUT = 1, 2
+NBINS, CELL = 59, 8
+
+_DT_NAMES = {"f32": DT_F32, "fp32": DT_F32, "bf16": DT_BF16, "fp8": DT_FP8, "e4m3": DT_FP8, "tf32": DT_TF32}
+_lib = None
+
+
+class RgbdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rgbd error {code}: {msg}")
+        self.code = code
+
+
+class SvmInfo(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n_sv", ctypes.c_int32),
+                ("n_sv_pad", ctypes.c_int32), ("dim", ctypes.c_int32), ("k_pad", ctypes.c_int32),
+                ("n_classes", ctypes.c_int32), ("scorable", ctypes.c_int32), ("gamma", ctypes.c_float),
+                ("sv_scale", ctypes.c_float)]
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions the C header declares."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*int\s+([a-z_0-9]+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """The loaded library; raises if it was not built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, F, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+        sig = {
+            "rgbd_version": [],
+            "rgbd_last_error": [P, Z],
+            "rgbd_ctx_create": [I, P],
+            "rgbd_ctx_destroy": [P],
+            "rgbd_ctx_reserve": [P, Z],
+            "rgbd_ctx_status": [P, P, I],
+            "rgbd_crop_affine": [P, P, P, I, I, I, P, P, I, I, I, P, P, P],
+            "lbp_fused_features": [P, P, P, I, I, I, P, P, I, I, I, I, I, P, I, P, I, F, P, P],
+            "lbp_normalize_features": [P, P, I, I, I, I, P, I, F, P, P],
+            "svm_train_data_pack": [P, P, I, I, I, P, P, I, I, F, I, P, P],
+            "rgbd_svm_free": [P],
+            "rgbd_svm_get_info": [P, P],
+            "rgbd_svm_packed_sv": [P, P, P],
+            "svm_score": [P, P, P, P, I, F, P, P, P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    lib().rgbd_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc):
+    if rc != RGBD_OK:
+        raise RgbdError(rc, last_error())
+
+
+def _p(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on the GPU")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dt(x):
+    if x is None or x == 0:
+        return 0
+    if isinstance(x, str):
+        return _DT_NAMES[x.lower()]
+    return int(x)
+
+
+def x_torch_dtype(dt):
+    dt = _dt(dt)
+    return {DT_F32: torch.float32, DT_TF32: torch.float32, DT_BF16: torch.bfloat16, DT_FP8: torch.uint8}[dt]
+
+
+def k_pad_for(dim: int) -> int:
+    return (dim + 127) // 128 * 128
+
+
+class Context:
+    """rgbd_ctx: status word and workspace of one device."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib().rgbd_ctx_create(device, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().rgbd_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, nbytes: int):
+        _check(lib().rgbd_ctx_reserve(self.handle, ctypes.c_size_t(nbytes)))
+
+    def status(self, clear: bool = True) -> int:
+        v = ctypes.c_uint32(0)
+        _check(lib().rgbd_ctx_status(self.handle, ctypes.byref(v), 1 if clear else 0))
+        return v.value
+
+
+def rects_tensor(rects, device="cuda"):
+    """rects: numpy structured array (frame, x, y, w, h) or an int array [n][5] -> int32 [n][5]."""
+    import numpy as np
+    if isinstance(rects, torch.Tensor):
+        return rects.to(device=device, dtype=torch.int32).contiguous()
+    a = np.asarray(rects)
+    if a.dtype.names:
+        a = np.stack([a[k] for k in ("frame", "x", "y", "w", "h")], axis=1)
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.int32), device=device)
+
+
+def rgbd_crop_affine(ctx, grey, depth, rects, out_h, out_w, affine=None, out_grey=None, out_depth=None,
+                     stream=None):
+    F, H, W = grey.shape
+    n = rects.shape[0]
+    if out_grey is None:
+        out_grey = torch.empty((n, out_h, out_w), dtype=torch.uint8, device=grey.device)
+    if out_depth is None:
+        out_depth = torch.empty((n, out_h, out_w), dtype=torch.int16, device=grey.device)
+    _check(lib().rgbd_crop_affine(ctx.handle, _p(grey), _p(depth), F, H, W, _p(rects), _p(affine), n, out_h,
+                                  out_w, _p(out_grey), _p(out_depth), _stream(stream)))
+    return out_grey, out_depth
+
+
+def lbp_fused_features(ctx, grey, depth, rects=None, crop=128, cell=CELL, mask_mm=150, flags=0, feats=True,
+                       x_dtype=0, k_pad=None, x_scale=448.0, xsq=True, affine=None, out=None, stream=None):
+    """Returns (feats uint16-as-int16 [n][dim] or None, x [n][k_pad] or None, xsq [n] or None)."""
+    F, H, W = grey.shape
+    n = F if rects is None else rects.shape[0]
+    dim = (crop // cell) ** 2 * NBINS
+    dt = _dt(x_dtype)
+    k_pad = k_pad_for(dim) if k_pad is None else k_pad
+    out = out or {}
+    f = out.get("feats")
+    if feats and f is None:
+        f = torch.empty((n, dim), dtype=torch.int16, device=grey.device)
+    x = out.get("x")
+    if dt and x is None:
+        x = torch.empty((n, k_pad), dtype=x_torch_dtype(dt), device=grey.device)
+    q = out.get("xsq")
+    if dt and xsq and q is None:
+        q = torch.empty((n,), dtype=torch.float32, device=grey.device)
+    _check(lib().lbp_fused_features(ctx.handle, _p(grey), _p(depth), F, H, W, _p(rects), _p(affine), n, crop, cell,
+                                    mask_mm, flags, _p(f) if feats else None, dt, _p(x) if dt else None, k_pad,
+                                    float(x_scale), _p(q) if (dt and xsq) else None, _stream(stream)))
+    return (f if feats else None), (x if dt else None), (q if (dt and xsq) else None)
+
+
+def lbp_normalize_features(ctx, feats, x_dtype, k_pad=None, x_scale=448.0, nbins=NBINS, stream=None):
+    n, dim = feats.shape
+    dt = _dt(x_dtype)
+    k_pad = k_pad_for(dim) if k_pad is None else k_pad
+    x = torch.empty((n, k_pad), dtype=x_torch_dtype(dt), device=feats.device)
+    q = torch.empty((n,), dtype=torch.float32, device=feats.device)
+    _check(lib().lbp_normalize_features(ctx.handle, _p(feats), n, dim, nbins, dt, _p(x), k_pad, float(x_scale),
+                                        _p(q), _stream(stream)))
+    return x, q
+
+
+class SvmModel:
+    """rgbd_svm: a packed, device-resident SVM."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        info = SvmInfo()
+        _check(lib().rgbd_svm_get_info(handle, ctypes.byref(info)))
+        self.info = info
+
+    @property
+    def k_pad(self):
+        return self.info.k_pad
+
+    @property
+    def dtype(self):
+        return self.info.dtype
+
+    def free(self):
+        if self.handle:
+            lib().rgbd_svm_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def svm_train_data_pack(ctx, sv_feats, coef, bias=None, kernel=KERNEL_RBF, gamma=None, dtype=DT_F32, dim=None,
+                        nbins=NBINS, stream=None):
+    if kernel == KERNEL_RBF:
+        n_sv, dim = sv_feats.shape
+        gamma = 1.0 / dim if gamma is None else gamma
+    else:
+        n_sv = 0
+        dim = coef.shape[1] if dim is None else dim
+        gamma = 0.0 if gamma is None else gamma
+    C = coef.shape[0] if coef is not None else 0
+    h = ctypes.c_void_p()
+    _check(lib().svm_train_data_pack(ctx.handle, _p(sv_feats) if sv_feats is not None else None, n_sv, dim, nbins,
+                                     _p(coef), _p(bias), C, kernel, float(gamma), _dt(dtype), ctypes.byref(h),
+                                     _stream(stream)))
+    return SvmModel(h)
+
+
+def svm_score(ctx, model, x, xsq=None, x_scale=448.0, scores=None, labels=None, want_labels=True, stream=None):
+    n = x.shape[0]
+    C = model.info.n_classes
+    if scores is None:
+        scores = torch.empty((n, C), dtype=torch.float32, device=x.device)
+    if want_labels and labels is None:
+        labels = torch.empty((n,), dtype=torch.int32, device=x.device)
+    _check(lib().svm_score(ctx.handle, model.handle, _p(x), _p(xsq), n, float(x_scale), _p(scores),
+                           _p(labels) if want_labels else None, _stream(stream)))
+    return scores, (labels if want_labels else None)

@@ -1,0 +1,130 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rgbd_lbp.h"
+
+namespace rgbd {
+
+constexpr int kBins = 59;     // uniform-pattern bins per cell (58 uniform + 1)
+constexpr int kCell = 8;      // cell side in pixels
+constexpr int kKAlign = 128;  // k_pad granularity (elements)
+
+// Sets the thread's last error message (printf-style) and returns `code`.
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+struct DeviceProps {
+    int device = 0;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t smem_optin = 0;
+};
+
+}  // namespace rgbd
+
+struct rgbd_ctx {
+    rgbd::DeviceProps props;
+    uint32_t* d_status = nullptr;  // device status word
+    void* workspace = nullptr;
+    size_t workspace_bytes = 0;
+};
+
+struct rgbd_svm {
+    int device = 0;
+    int kernel = RGBD_KERNEL_RBF;
+    int dtype = RGBD_DT_F32;
+    int n_sv = 0, n_pad = 0, dim = 0, nbins = rgbd::kBins, k_pad = 0;
+    int C = 0, C_pad = 0;
+    float gamma = 0.f;
+    float sv_scale = 1.f;
+    bool scorable = false;
+    void* sv = nullptr;       // [n_pad][k_pad] of dtype (float for F32 / TF32)
+    float* sv_sq = nullptr;   // [n_pad]
+    float* coef = nullptr;    // RBF: float [C][n_pad]; linear: float [C][k_pad]
+    uint16_t* coef_bf16 = nullptr;  // RBF tensor path: bf16 bits [C_pad][n_pad]
+    float* asum = nullptr;    // [C] sum_i a_ci (accumulated in fp64)
+    float* bias = nullptr;    // [C]
+    CUtensorMap tm_sv;        // tensor-core path: TMA descriptors
+    CUtensorMap tm_coef;
+    bool has_tmaps = false;
+};
+
+namespace rgbd {
+
+// RAII device selection: makes ctx's device current for the scope of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = (cudaSetDevice(dev) == cudaSuccess);
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+// Grows the workspace of ctx to `bytes`.  Refuses while `stream` is capturing.
+int ensure_workspace(rgbd_ctx* ctx, size_t bytes, cudaStream_t stream);
+
+// ---- launchers (each returns RGBD_OK or an error code with the message set) ----------
+int launch_crop_affine(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, int n_frames,
+                       int H, int W, const rgbd_rect* rects, const int32_t* affine, int n,
+                       int out_h, int out_w, uint8_t* og, uint16_t* od, cudaStream_t s);
+
+struct LbpArgs {
+    const uint8_t* grey;
+    const uint16_t* depth;
+    int n_frames, H, W;
+    const rgbd_rect* rects;
+    const int32_t* affine;
+    int n;
+    int crop;
+    int mask_mm;
+    int flags;
+    uint16_t* feats;
+    int x_dtype;
+    void* x_out;
+    int k_pad;
+    float x_scale;
+    float* xsq;
+    uint32_t* status;
+};
+int launch_lbp_fused(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s);
+
+int launch_normalize(const uint16_t* feats, int n, int dim, int nbins, int x_dtype, void* x_out,
+                     int k_pad, float x_scale, float* xsq, float* row_max, cudaStream_t s);
+
+int launch_quantize_f32(const float* src, int n, int k_pad, int x_dtype, void* dst, float scale,
+                        float* sq, cudaStream_t s);
+
+// scoring
+int score_linear(rgbd_ctx* ctx, const rgbd_svm* m, const float* x, int n, float* scores,
+                 int32_t* labels, cudaStream_t s);
+int score_rbf_f32(rgbd_ctx* ctx, const rgbd_svm* m, const float* x, const float* xsq, int n,
+                  float* scores, int32_t* labels, cudaStream_t s);
+int score_rbf_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n,
+                 float x_scale, float* scores, int32_t* labels, cudaStream_t s);
+
+// model packing helpers (pack.cu)
+int pack_model_tensor_maps(rgbd_svm* m);
+
+// Final reduction of per-split partial scores (svm_simt.cu), shared by both RBF paths.
+//   part  [splits][n][C_stride] partial sums D_s[k][c]
+//   ref   NULL, or [splits][n] per-split reference distances r_s (see svm_tc.cu)
+int launch_reduce_scores(const float* part, const float* ref, int splits, int n, int C,
+                         int C_stride, const float* asum, const float* asum_split,
+                         const float* bias, float gamma, float* scores, int32_t* labels,
+                         cudaStream_t s);
+
+// TMA descriptor encoding through the driver entry point (no libcuda link).
+int encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                   uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+                   CUtensorMapSwizzle swizzle);
+
+}  // namespace rgbd

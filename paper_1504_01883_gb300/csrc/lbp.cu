@@ -1,0 +1,697 @@
+// lbp.cu -- steps A1..A5 of the hot path on sm_103a:
+//   A1 affine crop of each face rect (Section 2.1, Eq. 1; Section 3 resizes every face),
+//   A2 median-depth mask (the depth/grey fusion of Sections 1 and 2.5),
+//   A3 8-neighbour radius-1 LBP codes (Section 2.4, Eq. 2, Fig. 7),
+//   A4 per-cell uniform-pattern histograms (Section 2.4, Eq. 3; Section 3),
+//   A5 per-cell normalisation (and bf16 / FP8 quantisation) of the feature rows.
+//
+// The fused kernel is persistent: one CTA per half-SM slot walks over faces.  Per face:
+//   P1  every thread resamples 8 groups of 4 crop pixels (grey bilinear, depth nearest);
+//       grey goes to shared memory, the 32 depth values stay in registers, and the
+//       high byte of each depth feeds a 256-bin histogram (warp-aggregated when a
+//       warp's values span at most two bins, as on a smooth face).
+//   P2/P3  radix select of the lower median: the high-byte bin holding rank (n-1)/2,
+//       then a low-byte histogram restricted to that bin.
+//   P4  mask bytes (0x80 = valid) from the registers.
+//   P5  one thread per half cell (4 x 8 pixels) walks down its 8 rows with a
+//       3-row sliding window of packed words and computes four codes per step
+//       with byte-SIMD compares; codes go through the uniform table into a
+//       thread-private 8-bit histogram (no atomics, no bank conflicts).
+//   P6/P7  half-cell histograms are summed into a uint16 staging row, which is
+//       written out coalesced together with the normalised row and its norm.
+// Everything up to A4 is exact integer arithmetic.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace rgbd {
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------------------
+// A1 helpers: Q16.16 source coordinates, pixel centre to pixel centre.
+// ---------------------------------------------------------------------------------------
+
+// origin + (i + 1/2) * len / out_len - 1/2 in Q16.16 (len > 0, so the quotient is >= 0).
+__device__ __forceinline__ int64_t rect_coord_q16(int origin, int len, int out_len, int i) {
+    uint64_t num = (uint64_t)(2 * i + 1) * (uint64_t)len * 65536ull;
+    return (int64_t)origin * 65536 + (int64_t)(num / (2ull * (uint64_t)out_len)) - 32768;
+}
+
+// Packs the taps of one coordinate: .x = a | (b - a) << 16 | frac << 24 (bilinear: clamped
+// taps a = floor, b = floor + 1, Q8 fraction), .y = the clamped nearest index.
+__device__ __forceinline__ uint2 make_tap(int64_t q, int lim) {
+    const int64_t f0 = q >> 16;  // floor (arithmetic shift)
+    const int frac = (int)((q >> 8) & 255);
+    const int64_t nn = (q + 32768) >> 16;
+    const int64_t hi = (int64_t)lim - 1;
+    const int a = (int)(f0 < 0 ? 0 : (f0 > hi ? hi : f0));
+    const int b = (int)(f0 + 1 < 0 ? 0 : (f0 + 1 > hi ? hi : f0 + 1));
+    const int n = (int)(nn < 0 ? 0 : (nn > hi ? hi : nn));
+    return make_uint2((uint32_t)a | ((uint32_t)(b - a) << 16) | ((uint32_t)frac << 24), (uint32_t)n);
+}
+
+// Bilinear grey sample with Q8 weights (they sum to 2^16), rounded half up.
+__device__ __forceinline__ uint32_t bilerp(const uint8_t* img, int W, uint32_t cx, uint32_t ry) {
+    const uint32_t xa = cx & 0xFFFFu, dx = (cx >> 16) & 1u, fx = cx >> 24;
+    const uint32_t ya = ry & 0xFFFFu, dy = (ry >> 16) & 1u, fy = ry >> 24;
+    const uint8_t* r0 = img + (size_t)ya * W + xa;
+    const uint8_t* r1 = r0 + (size_t)dy * W;
+    const uint32_t p00 = __ldg(r0), p01 = __ldg(r0 + dx);
+    const uint32_t p10 = __ldg(r1), p11 = __ldg(r1 + dx);
+    const uint32_t acc = (256u - fy) * ((256u - fx) * p00 + fx * p01) + fy * ((256u - fx) * p10 + fx * p11);
+    return (acc + 32768u) >> 16;
+}
+
+// ---------------------------------------------------------------------------------------
+// A3 helper: byte-SIMD "a > b" (or >=) on four packed pixels.  cb = (b & 0x7f7f7f7f) + 1 per
+// byte for the strict test, without the +1 for >=.  Result: 0x80 in each byte where it holds.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cmp_msb(uint32_t a, uint32_t b, uint32_t cb) {
+    const uint32_t d = (a | 0x80808080u) - cb;  // per byte: low 7 bits of a vs b, no borrows
+    return ((a & ~b) | (~(a ^ b) & d)) & 0x80808080u;
+}
+
+template <int S>
+struct Cfg {
+    static constexpr int G = S / 8;          // cells per side
+    static constexpr int NT = 2 * G * G;     // threads: one per half cell
+    static constexpr int SW = S / 4;         // packed words per crop row
+    static constexpr int DIM = G * G * kBins;
+    static constexpr int HW = 15;            // histogram words per thread (60 bins / 4)
+    static constexpr int MINB = (S == 128) ? 2 : 1;
+};
+
+template <int S>
+struct __align__(16) Smem {
+    uint32_t img[2 * S * S / 4];       // grey words, then mask words; later the uint16 staging row
+    uint32_t hist[Cfg<S>::HW * Cfg<S>::NT];  // thread-private 8-bit counts, word (bin/4)*NT + t
+    uint2 colmap[S];                   // taps per crop column, index (u % 4) * SW + u / 4
+    uint2 rowmap[S];                   // taps per crop row
+    uint32_t h1[256];                  // depth high-byte histogram
+    uint32_t h2[256];                  // depth low-byte histogram inside the median's bin
+    uint32_t cnt[Cfg<S>::NT];          // valid centres per half cell
+    float red[Cfg<S>::NT / 32];
+    int info[4];
+    uint8_t lut[256];                  // uniform-pattern bin of each code
+};
+
+template <int S>
+__global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(LbpArgs a) {
+    using C = Cfg<S>;
+    constexpr int NT = C::NT, SW = C::SW, G = C::G, DIM = C::DIM;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<S>& sm = *reinterpret_cast<Smem<S>*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // Uniform-pattern table: code c is uniform when it has at most two 0/1 changes around the
+    // ring; uniform codes are ranked in ascending order (0..57), all others share bin 58.
+    if (warp == 0) {
+        int prefix = 0;
+        for (int r = 0; r < 8; ++r) {
+            const int c = r * 32 + lane;
+            const int rot = ((c << 1) | (c >> 7)) & 0xFF;
+            const bool uni = __popc(c ^ rot) <= 2;
+            const unsigned m = __ballot_sync(FULL, uni);
+            const int rank = prefix + __popc(m & ((1u << lane) - 1u));
+            sm.lut[c] = (uint8_t)(uni ? rank : 58);
+            prefix += __popc(m);
+        }
+    }
+
+    const bool strict = !(a.flags & RGBD_LBP_GE);
+    const bool nbr_ignore = (a.flags & RGBD_LBP_NBR_IGNORE_MASK) != 0;
+    const int x_dtype = a.x_out ? a.x_dtype : 0;
+
+    for (int face = blockIdx.x; face < a.n; face += gridDim.x) {
+        __syncthreads();  // the previous face's output pass is done with shared memory
+
+        // ---- P0: descriptor, tap maps, cleared histograms --------------------------------
+        bool ok = true;
+        rgbd_rect r = {0, 0, 0, S, S};
+        const uint8_t* gsrc = a.grey;
+        const uint16_t* dsrc = a.depth;
+        int64_t aff[6] = {0, 0, 0, 0, 0, 0};
+        if (a.rects) {
+            r = a.rects[face];
+            ok = r.frame >= 0 && r.frame < a.n_frames && r.w > 0 && r.h > 0;
+            if (!ok && tid == 0) atomicOr(a.status, RGBD_STATUS_BAD_RECT);
+            if (ok) {
+                gsrc += (size_t)r.frame * a.H * a.W;
+                dsrc += (size_t)r.frame * a.H * a.W;
+            }
+            if (ok && a.affine) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) aff[i] = a.affine[6 * (size_t)face + i];
+            } else if (ok) {
+                for (int i = tid; i < 2 * S; i += NT) {
+                    if (i < S) {
+                        sm.colmap[(i & 3) * SW + (i >> 2)] = make_tap(rect_coord_q16(r.x, r.w, S, i), a.W);
+                    } else {
+                        const int v = i - S;
+                        sm.rowmap[v] = make_tap(rect_coord_q16(r.y, r.h, S, v), a.H);
+                    }
+                }
+            }
+        } else {
+            gsrc += (size_t)face * S * S;
+            dsrc += (size_t)face * S * S;
+        }
+        for (int i = tid; i < 256; i += NT) {
+            sm.h1[i] = 0;
+            sm.h2[i] = 0;
+        }
+#pragma unroll
+        for (int w = 0; w < C::HW; ++w) sm.hist[w * NT + tid] = 0;
+        __syncthreads();
+
+        // ---- P1: resample; grey to shared memory, depth to registers ----------------------
+        uint32_t dreg[16];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int item = tid + k * NT;  // = v * SW + q
+            const int v = item / SW, q = item - v * SW;
+            uint32_t gw = 0, d01 = 0, d23 = 0;
+            if (ok) {
+                if (!a.rects) {
+                    gw = __ldg(reinterpret_cast<const uint32_t*>(gsrc) + item);
+                    const uint2 dd = __ldg(reinterpret_cast<const uint2*>(dsrc) + item);
+                    d01 = dd.x;
+                    d23 = dd.y;
+                } else if (!a.affine) {
+                    const uint2 rm = sm.rowmap[v];
+                    const uint16_t* drow = dsrc + (size_t)rm.y * a.W;
+                    uint32_t dv[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const uint2 cm = sm.colmap[e * SW + q];
+                        gw |= bilerp(gsrc, a.W, cm.x, rm.x) << (8 * e);
+                        dv[e] = __ldg(drow + cm.y);
+                    }
+                    d01 = dv[0] | (dv[1] << 16);
+                    d23 = dv[2] | (dv[3] << 16);
+                } else {
+                    uint32_t dv[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int u = 4 * q + e;
+                        const int64_t xq = aff[0] * u + aff[1] * v + aff[2];
+                        const int64_t yq = aff[3] * u + aff[4] * v + aff[5];
+                        const uint2 tx = make_tap(xq, a.W), ty = make_tap(yq, a.H);
+                        gw |= bilerp(gsrc, a.W, tx.x, ty.x) << (8 * e);
+                        dv[e] = __ldg(dsrc + (size_t)ty.y * a.W + tx.y);
+                    }
+                    d01 = dv[0] | (dv[1] << 16);
+                    d23 = dv[2] | (dv[3] << 16);
+                }
+            }
+            sm.img[item] = gw;
+            dreg[2 * k] = d01;
+            dreg[2 * k + 1] = d23;
+
+            // high-byte histogram of the non-zero depths
+            const uint32_t dv4[4] = {d01 & 0xFFFFu, d01 >> 16, d23 & 0xFFFFu, d23 >> 16};
+            int kmin = 256, kmax = -1;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (dv4[e]) {
+                    const int key = (int)(dv4[e] >> 8);
+                    kmin = min(kmin, key);
+                    kmax = max(kmax, key);
+                }
+            }
+            const int wmin = __reduce_min_sync(FULL, kmin);
+            const int wmax = __reduce_max_sync(FULL, kmax);
+            if (wmax >= 0) {
+                if (wmax - wmin <= 1) {
+                    unsigned clo = 0, chi = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (dv4[e]) {
+                            const int key = (int)(dv4[e] >> 8);
+                            clo += key == wmin;
+                            chi += (key == wmax) && (wmax != wmin);
+                        }
+                    }
+                    const unsigned tlo = __reduce_add_sync(FULL, clo);
+                    const unsigned thi = __reduce_add_sync(FULL, chi);
+                    if (lane == 0) {
+                        atomicAdd(&sm.h1[wmin], tlo);
+                        if (thi) atomicAdd(&sm.h1[wmax], thi);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (dv4[e]) atomicAdd(&sm.h1[dv4[e] >> 8], 1u);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- P2: high-byte bin of the lower median (rank (n-1)/2 of the non-zero depths) ---
+        if (warp == 0) {
+            uint32_t s8[8], lsum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                s8[j] = sm.h1[lane * 8 + j];
+                lsum += s8[j];
+            }
+            uint32_t incl = lsum;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, incl, off);
+                if (lane >= off) incl += t;
+            }
+            const uint32_t total = __shfl_sync(FULL, incl, 31);
+            int b1 = -1, k1 = 0;
+            if (total > 0) {
+                const uint32_t k = (total - 1) / 2;
+                const uint32_t excl = incl - lsum;
+                const unsigned m = __ballot_sync(FULL, k >= excl && k < incl);
+                const int src = __ffs(m) - 1;
+                if (lane == src) {
+                    uint32_t c = excl;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (b1 < 0 && k < c + s8[j]) {
+                            b1 = lane * 8 + j;
+                            k1 = (int)(k - c);
+                        }
+                        c += s8[j];
+                    }
+                }
+                b1 = __shfl_sync(FULL, b1, src);
+                k1 = __shfl_sync(FULL, k1, src);
+            }
+            if (lane == 0) {
+                sm.info[0] = b1;
+                sm.info[1] = k1;
+            }
+        }
+        __syncthreads();
+        const int b1 = sm.info[0];
+
+        // ---- P3: low byte of the median inside bin b1 ------------------------------------
+        int med = -1;
+        if (b1 >= 0) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t lo = dreg[i] & 0xFFFFu, hi = dreg[i] >> 16;
+                if (lo && (int)(lo >> 8) == b1) atomicAdd(&sm.h2[lo & 255u], 1u);
+                if (hi && (int)(hi >> 8) == b1) atomicAdd(&sm.h2[hi & 255u], 1u);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t k1 = (uint32_t)sm.info[1];
+                uint32_t s8[8], lsum = 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    s8[j] = sm.h2[lane * 8 + j];
+                    lsum += s8[j];
+                }
+                uint32_t incl = lsum;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t t = __shfl_up_sync(FULL, incl, off);
+                    if (lane >= off) incl += t;
+                }
+                const uint32_t excl = incl - lsum;
+                const unsigned m = __ballot_sync(FULL, k1 >= excl && k1 < incl);
+                const int src = __ffs(m) - 1;
+                int b2 = -1;
+                if (lane == src) {
+                    uint32_t c = excl;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (b2 < 0 && k1 < c + s8[j]) b2 = lane * 8 + j;
+                        c += s8[j];
+                    }
+                }
+                b2 = __shfl_sync(FULL, b2, src);
+                if (lane == 0) sm.info[2] = b1 * 256 + b2;
+            }
+            __syncthreads();
+            med = sm.info[2];
+        }
+
+        // ---- P4: depth mask, 0x80 per valid pixel ----------------------------------------
+        {
+            uint32_t* mw = sm.img + S * S / 4;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                uint32_t m = 0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int d = (int)((dreg[2 * k + (e >> 1)] >> (16 * (e & 1))) & 0xFFFFu);
+                    const int diff = d - med;
+                    const bool valid = med >= 0 && d != 0 && diff < a.mask_mm && -diff < a.mask_mm;
+                    m |= valid ? (0x80u << (8 * e)) : 0u;
+                }
+                mw[tid + k * NT] = m;
+            }
+        }
+        __syncthreads();
+
+        // ---- P5: LBP codes and private histograms, one half cell per thread ---------------
+        {
+            const int c = tid >> 1, h = tid & 1;
+            const int cy = c / G, cx = c - cy * G;
+            const int wc = 2 * cx + h;
+            const int r0 = 8 * cy;
+            const bool le = wc == 0, re = wc == SW - 1;
+            const int wl = le ? wc : wc - 1, wr = re ? wc : wc + 1;
+            const uint32_t* GW = sm.img;
+            const uint32_t* MW = sm.img + S * S / 4;
+            // Words holding pixels (x-1 .. x+2), (x .. x+3), (x+1 .. x+4) of a row; past the crop
+            // edge a neighbour repeats the edge pixel.
+            auto row3 = [&](const uint32_t* base, int row, uint32_t& L, uint32_t& M, uint32_t& R) {
+                row = min(max(row, 0), S - 1);
+                const uint32_t* p = base + row * SW;
+                const uint32_t c0 = p[wc];
+                const uint32_t l0 = le ? (c0 << 24) : p[wl];
+                const uint32_t r1 = re ? (c0 >> 24) : p[wr];
+                L = __byte_perm(l0, c0, 0x6543);
+                M = c0;
+                R = __byte_perm(c0, r1, 0x4321);
+            };
+            uint32_t gUL, gUC, gUR, gCL, gCC, gCR, gDL, gDC, gDR;
+            uint32_t mUL, mUC, mUR, mCL, mCC, mCR, mDL, mDC, mDR;
+            row3(GW, r0 - 1, gUL, gUC, gUR);
+            row3(MW, r0 - 1, mUL, mUC, mUR);
+            row3(GW, r0, gCL, gCC, gCR);
+            row3(MW, r0, mCL, mCC, mCR);
+            uint32_t nvalid = 0;
+            uint8_t* hb = reinterpret_cast<uint8_t*>(sm.hist);
+#pragma unroll 2
+            for (int i = 0; i < 8; ++i) {
+                row3(GW, r0 + i + 1, gDL, gDC, gDR);
+                row3(MW, r0 + i + 1, mDL, mDC, mDR);
+                const uint32_t NM = 0x80808080u;
+                const uint32_t cb = (gCC & 0x7F7F7F7Fu) + (strict ? 0x01010101u : 0u);
+                const uint32_t code =
+                    ((cmp_msb(gUL, gCC, cb) & (nbr_ignore ? NM : mUL)) >> 7) |
+                    ((cmp_msb(gUC, gCC, cb) & (nbr_ignore ? NM : mUC)) >> 6) |
+                    ((cmp_msb(gUR, gCC, cb) & (nbr_ignore ? NM : mUR)) >> 5) |
+                    ((cmp_msb(gCR, gCC, cb) & (nbr_ignore ? NM : mCR)) >> 4) |
+                    ((cmp_msb(gDR, gCC, cb) & (nbr_ignore ? NM : mDR)) >> 3) |
+                    ((cmp_msb(gDC, gCC, cb) & (nbr_ignore ? NM : mDC)) >> 2) |
+                    ((cmp_msb(gDL, gCC, cb) & (nbr_ignore ? NM : mDL)) >> 1) |
+                    (cmp_msb(gCL, gCC, cb) & (nbr_ignore ? NM : mCL));
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if ((mCC >> (8 * e + 7)) & 1u) {
+                        const int bin = sm.lut[(code >> (8 * e)) & 0xFFu];
+                        hb[((bin >> 2) * NT + tid) * 4 + (bin & 3)] += 1;
+                        ++nvalid;
+                    }
+                }
+                gUL = gCL; gUC = gCC; gUR = gCR; gCL = gDL; gCC = gDC; gCR = gDR;
+                mUL = mCL; mUC = mCC; mUR = mCR; mCL = mDL; mCC = mDC; mCR = mDR;
+            }
+            sm.cnt[tid] = nvalid;
+        }
+        __syncthreads();
+
+        // ---- P6: sum the two half-cell histograms into a uint16 staging row ----------------
+        uint16_t* stg = reinterpret_cast<uint16_t*>(sm.img);
+        {
+            const int c = tid >> 1, h = tid & 1;
+            const int w0 = h ? 8 : 0, w1 = h ? C::HW : 8;
+            for (int w = w0; w < w1; ++w) {
+                const uint32_t s = sm.hist[w * NT + 2 * c] + sm.hist[w * NT + 2 * c + 1];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int b = 4 * w + e;
+                    if (b < kBins) stg[c * kBins + b] = (uint16_t)((s >> (8 * e)) & 0xFFu);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- P7: coalesced output of counts, normalised row and its squared norm ----------
+        float sq = 0.f;
+        const int len4 = (x_dtype ? a.k_pad : DIM) / 4;
+        for (int j4 = tid; j4 < len4; j4 += NT) {
+            const int j = 4 * j4;
+            uint2 hv = make_uint2(0, 0);
+            if (j < DIM) {
+                hv = *reinterpret_cast<const uint2*>(stg + j);
+                if (a.feats) *reinterpret_cast<uint2*>(a.feats + (size_t)face * DIM + j) = hv;
+            }
+            if (x_dtype) {
+                float x[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int jj = j + e;
+                    x[e] = 0.f;
+                    if (jj < DIM) {
+                        const int cc = jj / kBins;
+                        const uint32_t nv = sm.cnt[2 * cc] + sm.cnt[2 * cc + 1];
+                        const uint32_t hc = ((e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0xFFFFu;
+                        x[e] = nv ? (float)hc / (float)nv : 0.f;
+                    }
+                }
+                if (x_dtype == RGBD_DT_BF16) {
+                    uint32_t pk[2];
+#pragma unroll
+                    for (int e = 0; e < 4; e += 2) {
+                        const __nv_bfloat16 q0 = __float2bfloat16_rn(x[e]);
+                        const __nv_bfloat16 q1 = __float2bfloat16_rn(x[e + 1]);
+                        const float f0 = __bfloat162float(q0), f1 = __bfloat162float(q1);
+                        sq = fmaf(f0, f0, sq);
+                        sq = fmaf(f1, f1, sq);
+                        pk[e >> 1] = (uint32_t)__bfloat16_as_ushort(q0) |
+                                     ((uint32_t)__bfloat16_as_ushort(q1) << 16);
+                    }
+                    *reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(a.x_out) +
+                                              (size_t)face * a.k_pad + j) = make_uint2(pk[0], pk[1]);
+                } else if (x_dtype == RGBD_DT_FP8) {
+                    uint32_t pk = 0;
+                    const float inv = 1.0f / a.x_scale;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __nv_fp8_e4m3 q8(x[e] * a.x_scale);
+                        const float f = static_cast<float>(q8) * inv;
+                        sq = fmaf(f, f, sq);
+                        pk |= (uint32_t)q8.__x << (8 * e);
+                    }
+                    *reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(a.x_out) +
+                                                 (size_t)face * a.k_pad + j) = pk;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) sq = fmaf(x[e], x[e], sq);
+                    *reinterpret_cast<float4*>(reinterpret_cast<float*>(a.x_out) +
+                                               (size_t)face * a.k_pad + j) =
+                        make_float4(x[0], x[1], x[2], x[3]);
+                }
+            }
+        }
+        if (a.xsq) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(FULL, sq, off);
+            if (lane == 0) sm.red[warp] = sq;
+            __syncthreads();
+            if (tid == 0) {
+                float t = 0.f;
+                for (int w = 0; w < NT / 32; ++w) t += sm.red[w];
+                a.xsq[face] = t;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Plain crop (rgbd_crop_affine): one thread per crop pixel.
+// ---------------------------------------------------------------------------------------
+__global__ void crop_affine_kernel(const uint8_t* __restrict__ grey, const uint16_t* __restrict__ depth,
+                                   int n_frames, int H, int W, const rgbd_rect* __restrict__ rects,
+                                   const int32_t* __restrict__ affine, int n, int oh, int ow,
+                                   uint8_t* __restrict__ og, uint16_t* __restrict__ od,
+                                   uint32_t* status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= oh * ow) return;
+    const int v = p / ow, u = p - v * ow;
+    for (int k = blockIdx.y; k < n; k += gridDim.y) {
+        const rgbd_rect r = rects[k];
+        const size_t o = (size_t)k * oh * ow + p;
+        if (!(r.frame >= 0 && r.frame < n_frames && r.w > 0 && r.h > 0)) {
+            og[o] = 0;
+            od[o] = 0;
+            if (p == 0) atomicOr(status, RGBD_STATUS_BAD_RECT);
+            continue;
+        }
+        int64_t xq, yq;
+        if (affine) {
+            const int32_t* m = affine + 6 * (size_t)k;
+            xq = (int64_t)m[0] * u + (int64_t)m[1] * v + m[2];
+            yq = (int64_t)m[3] * u + (int64_t)m[4] * v + m[5];
+        } else {
+            xq = rect_coord_q16(r.x, r.w, ow, u);
+            yq = rect_coord_q16(r.y, r.h, oh, v);
+        }
+        const uint2 tx = make_tap(xq, W), ty = make_tap(yq, H);
+        const size_t base = (size_t)r.frame * H * W;
+        og[o] = (uint8_t)bilerp(grey + base, W, tx.x, ty.x);
+        od[o] = __ldg(depth + base + (size_t)ty.y * W + tx.y);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// A5 alone: per-cell normalisation of count rows; one CTA per row.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float store_x(void* out, int dtype, size_t idx, float x, float scale) {
+    if (dtype == RGBD_DT_BF16) {
+        const __nv_bfloat16 q = __float2bfloat16_rn(x);
+        reinterpret_cast<uint16_t*>(out)[idx] = __bfloat16_as_ushort(q);
+        return __bfloat162float(q);
+    } else if (dtype == RGBD_DT_FP8) {
+        const __nv_fp8_e4m3 q(x * scale);
+        reinterpret_cast<uint8_t*>(out)[idx] = q.__x;
+        return static_cast<float>(q) * (1.0f / scale);
+    }
+    reinterpret_cast<float*>(out)[idx] = x;
+    return x;
+}
+
+__global__ void normalize_kernel(const uint16_t* __restrict__ feats, int n, int dim, int nbins,
+                                 int x_dtype, void* x_out, int k_pad, float x_scale, float* xsq,
+                                 float* row_max) {
+    extern __shared__ uint32_t nv[];  // [dim / nbins]
+    __shared__ float red[2][32];
+    const int cells = dim / nbins;
+    for (int row = blockIdx.x; row < n; row += gridDim.x) {
+        __syncthreads();
+        const uint16_t* h = feats + (size_t)row * dim;
+        for (int c = threadIdx.x; c < cells; c += blockDim.x) {
+            uint32_t t = 0;
+            for (int b = 0; b < nbins; ++b) t += h[c * nbins + b];
+            nv[c] = t;
+        }
+        __syncthreads();
+        float sq = 0.f, mx = 0.f;
+        for (int j = threadIdx.x; j < k_pad; j += blockDim.x) {
+            float x = 0.f;
+            if (j < dim) {
+                const uint32_t t = nv[j / nbins];
+                x = t ? (float)h[j] / (float)t : 0.f;
+            }
+            mx = fmaxf(mx, x);
+            const float q = store_x(x_out, x_dtype, (size_t)row * k_pad + j, x, x_scale);
+            sq = fmaf(q, q, sq);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            sq += __shfl_xor_sync(FULL, sq, off);
+            mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[0][warp] = sq;
+            red[1][warp] = mx;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f, m = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                t += red[0][w];
+                m = fmaxf(m, red[1][w]);
+            }
+            if (xsq) xsq[row] = t;
+            if (row_max) atomicMax(reinterpret_cast<int*>(row_max), __float_as_int(m));  // m >= 0
+        }
+    }
+}
+
+// fp32 rows -> dtype rows (FP8 with `scale`), with squared norms of the stored values.
+__global__ void quantize_kernel(const float* __restrict__ src, int n, int k_pad, int dtype, void* dst,
+                                float scale, float* sq_out) {
+    __shared__ float red[32];
+    for (int row = blockIdx.x; row < n; row += gridDim.x) {
+        __syncthreads();
+        float sq = 0.f;
+        for (int j = threadIdx.x; j < k_pad; j += blockDim.x) {
+            const float q = store_x(dst, dtype, (size_t)row * k_pad + j, src[(size_t)row * k_pad + j], scale);
+            sq = fmaf(q, q, sq);
+        }
+        for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(FULL, sq, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            if (sq_out) sq_out[row] = t;
+        }
+    }
+}
+
+template <int S>
+int launch_fused_t(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
+    static int blocks_per_sm = -1;
+    const size_t smem = sizeof(Smem<S>);
+    if (blocks_per_sm < 0) {
+        cudaError_t e = cudaFuncSetAttribute(lbp_fused_kernel<S>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: smem attribute");
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lbp_fused_kernel<S>, Cfg<S>::NT, smem);
+        if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: occupancy");
+        blocks_per_sm = b > 0 ? b : 1;
+    }
+    const int grid = (int)std::min<long long>((long long)a.n, (long long)blocks_per_sm * ctx->props.sm_count);
+    lbp_fused_kernel<S><<<grid, Cfg<S>::NT, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: launch");
+    return RGBD_OK;
+}
+
+}  // namespace
+
+int launch_lbp_fused(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
+    switch (a.crop) {
+        case 32: return launch_fused_t<32>(ctx, a, s);
+        case 64: return launch_fused_t<64>(ctx, a, s);
+        case 96: return launch_fused_t<96>(ctx, a, s);
+        case 128: return launch_fused_t<128>(ctx, a, s);
+        default:
+            return set_error(RGBD_ERR_UNSUPPORTED, "lbp_fused_features: crop %d (32, 64, 96 or 128)", a.crop);
+    }
+}
+
+int launch_crop_affine(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, int n_frames,
+                       int H, int W, const rgbd_rect* rects, const int32_t* affine, int n,
+                       int out_h, int out_w, uint8_t* og, uint16_t* od, cudaStream_t s) {
+    const int px = out_h * out_w;
+    dim3 grid((px + 255) / 256, std::min(n, 65535));
+    crop_affine_kernel<<<grid, 256, 0, s>>>(grey, depth, n_frames, H, W, rects, affine, n, out_h,
+                                            out_w, og, od, ctx->d_status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "rgbd_crop_affine: launch");
+    return RGBD_OK;
+}
+
+int launch_normalize(const uint16_t* feats, int n, int dim, int nbins, int x_dtype, void* x_out,
+                     int k_pad, float x_scale, float* xsq, float* row_max, cudaStream_t s) {
+    const int cells = dim / nbins;
+    const size_t smem = sizeof(uint32_t) * (size_t)cells;
+    if (smem > 48 * 1024) return set_error(RGBD_ERR_UNSUPPORTED, "normalize: %d cells", cells);
+    const int grid = std::min(n, 8192);
+    normalize_kernel<<<grid, 256, smem, s>>>(feats, n, dim, nbins, x_dtype, x_out, k_pad, x_scale,
+                                             xsq, row_max);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "lbp_normalize_features: launch");
+    return RGBD_OK;
+}
+
+int launch_quantize_f32(const float* src, int n, int k_pad, int x_dtype, void* dst, float scale,
+                        float* sq, cudaStream_t s) {
+    const int grid = std::min(n, 8192);
+    quantize_kernel<<<grid, 256, 0, s>>>(src, n, k_pad, x_dtype, dst, scale, sq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "quantize: launch");
+    return RGBD_OK;
+}
+
+}  // namespace rgbd

@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Integer outputs (crops, LBP histograms) and the IEEE-division fp32 / bf16 / FP8 normalised
+rows must match bit for bit.  fp32 scores must agree with the fp64 oracle within 1e-5 of
+sum_i |a_ci| K_i + |b_c| (the oracle's score can be near zero when sum_i a_ci = 0).
+"""
+import numpy as np
+import pytest
+
+from paper_1504_01883_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1504_01883_gb300 import _build, binding
+    _build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+from gpu_util import dev_f32, dev_u16, dev_u8, host_bits32, host_u16, rbf_error_scale, rel_score_error  # noqa: E402
+
+
+# ---------------------------------------------------------------------------------------------
+# A1-A5 on the three crop layouts
+# ---------------------------------------------------------------------------------------------
+
+def test_plain_64_crop_features_and_linear_svm(B, ctx, orc):
+    wl = synth.plain_crop()
+    want = orc.features_batch(wl.grey, wl.depth, None, 64)
+    f, x, q = B.lbp_fused_features(ctx, dev_u8(wl.grey), dev_u16(wl.depth), None, crop=64, x_dtype="f32")
+    torch.cuda.synchronize()
+    assert (host_u16(f) == want).all()
+    x32 = orc.normalize_f32(want)
+    xh = x.cpu().numpy()
+    assert (xh[:, :3776].view(np.uint32) == x32.view(np.uint32)).all()
+    assert (xh[:, 3776:] == 0).all() and xh.shape[1] == 3840
+    assert np.allclose(q.cpu().numpy(), (x32.astype(np.float64) ** 2).sum(1), rtol=1e-6)
+    model = B.svm_train_data_pack(ctx, None, dev_f32(wl.coef), dev_f32(wl.bias), kernel=B.KERNEL_LINEAR, dim=3776)
+    s, lab = B.svm_score(ctx, model, x, q)
+    x64 = orc.normalize_f64(want)
+    ref = orc.svm_linear(x64, wl.coef, wl.bias)
+    scale = np.abs(x64) @ np.abs(wl.coef.astype(np.float64)).T + np.abs(wl.bias)[None, :]
+    assert np.all(np.abs(s.cpu().numpy() - ref) <= 1e-5 * scale)
+    assert (lab.cpu().numpy() == orc.argmax(ref)).all()
+    assert ctx.status() == 0
+
+
+def test_single_frame_crops_features_and_rbf_f32(B, ctx, orc):
+    wl = synth.single_frame()
+    g, d, r = dev_u8(wl.grey), dev_u16(wl.depth), B.rects_tensor(wl.rects)
+    cg, cd = B.rgbd_crop_affine(ctx, g, d, r, 128, 128)
+    for k, rr in enumerate(wl.rects):
+        og, od = orc.crop(wl.grey[rr["frame"]], wl.depth[rr["frame"]], (rr["x"], rr["y"], rr["w"], rr["h"]), 128, 128)
+        assert (cg[k].cpu().numpy() == og).all()
+        assert (host_u16(cd[k]) == od).all()
+    want = orc.features_batch(wl.grey, wl.depth, wl.rects, 128)
+    f, x, q = B.lbp_fused_features(ctx, g, d, r, crop=128, x_dtype="f32")
+    assert (host_u16(f) == want).all()
+    sv = dev_u16(wl.sv_counts)
+    model = B.svm_train_data_pack(ctx, sv, dev_f32(wl.coef), dev_f32(wl.bias), gamma=wl.gamma, dtype="f32")
+    s, lab = B.svm_score(ctx, model, x, q)
+    x64, sv64 = orc.normalize_f64(want), orc.normalize_f64(wl.sv_counts)
+    ref = orc.svm_rbf(x64, sv64, wl.coef, wl.bias, wl.gamma)
+    err = rel_score_error(s.cpu().numpy(), ref, rbf_error_scale(x64, sv64, wl.coef, wl.bias, wl.gamma))
+    assert err <= 1e-5, err
+    assert (lab.cpu().numpy() == orc.argmax(ref)).all()
+
+
+def _edge_frames():
+    """Ragged rect sizes (4..300 px, partly outside the frame), an all-hole frame, a rect on
+    background only, and two invalid descriptors."""
+    g, d, r = synth.frames_with_rects(99, 4, [5, 3, 6, 4], 4, 300, H=240, W=320)
+    d[2][:] = 0  # every rect of frame 2 is all holes
+    extra = np.zeros(4, synth.RECT_DTYPE)
+    extra[0] = (1, 250, 10, 60, 60)   # background-only region (may overlap nothing)
+    extra[1] = (0, -50, -40, 30, 30)  # entirely outside the frame: clamped edge pixels
+    extra[2] = (7, 10, 10, 50, 50)    # frame index out of range
+    extra[3] = (1, 10, 10, 0, 40)     # zero width
+    return g, d, np.concatenate([r, extra])
+
+
+@pytest.mark.parametrize("crop", [32, 64, 96, 128])
+def test_ragged_batch_and_edge_cases(B, ctx, orc, crop):
+    g, d, r = _edge_frames()
+    want = orc.features_batch(g, d, r, crop)
+    ctx.status(clear=True)
+    f, x, q = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=crop, x_dtype="f32")
+    got = host_u16(f)
+    assert (got == want).all(), np.nonzero((got != want).any(1))
+    assert not got[-2:].any()
+    assert ctx.status() & B.STATUS_BAD_RECT
+    x32 = orc.normalize_f32(want)
+    dim = want.shape[1]
+    assert (x.cpu().numpy()[:, :dim].view(np.uint32) == x32.view(np.uint32)).all()
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_lbp_option_flags(B, ctx, orc, flags):
+    g, d, r = synth.frames_with_rects(5, 2, 4, 40, 200, H=240, W=320)
+    want = orc.features_batch(g, d, r, 64, flags=flags)
+    f, _, _ = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=64, flags=flags)
+    assert (host_u16(f) == want).all()
+
+
+def test_general_affine_q16(B, ctx, orc):
+    g, d, r = synth.frames_with_rects(8, 2, 3, 60, 160, H=240, W=320)
+    n = r.shape[0]
+    rng = np.random.default_rng(1)
+    aff = np.zeros((n, 6), np.int32)
+    for k in range(n):
+        th = rng.uniform(-0.4, 0.4)
+        s = r[k]["w"] / 96.0
+        c, sn = np.cos(th) * s, np.sin(th) * s
+        aff[k] = [int(c * 65536), int(-sn * 65536), int(r[k]["x"] * 65536),
+                  int(sn * 65536), int(c * 65536), int(r[k]["y"] * 65536)]
+    want = orc.features_batch(g, d, r, 96, affine=aff)
+    f, _, _ = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=96,
+                                   affine=torch.from_numpy(aff).cuda())
+    assert (host_u16(f) == want).all()
+    cg, cd = B.rgbd_crop_affine(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), 96, 96, affine=torch.from_numpy(aff).cuda())
+    for k in range(n):
+        og, od = orc.crop(g[r[k]["frame"]], d[r[k]["frame"]], (0, 0, 1, 1), 96, 96, affine=aff[k])
+        assert (cg[k].cpu().numpy() == og).all() and (host_u16(cd[k]) == od).all()
+
+
+def test_quantised_rows_bit_exact(B, ctx, orc):
+    g, d, r = synth.frames_with_rects(12, 2, 5, 48, 256)
+    want = orc.features_batch(g, d, r, 128)
+    x32 = orc.normalize_f32(want)
+    dim = want.shape[1]
+    _, xb, qb = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=128, feats=False,
+                                     x_dtype="bf16")
+    assert (xb.view(torch.int16).cpu().numpy().view(np.uint16)[:, :dim] == orc.f32_to_bf16(x32)).all()
+    scale = np.float32(448.0)
+    _, x8, q8 = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=128, feats=False,
+                                     x_dtype="fp8", x_scale=float(scale))
+    codes = orc.f32_to_e4m3((x32 * scale).astype(np.float32))
+    assert (x8.cpu().numpy()[:, :dim] == codes).all()
+    back = orc.e4m3_to_f64(codes) / float(scale)
+    assert np.allclose(q8.cpu().numpy(), (back ** 2).sum(1), rtol=1e-5)
+    # the same rows from stored counts (lbp_normalize_features)
+    xn, _ = B.lbp_normalize_features(ctx, dev_u16(want), "bf16")
+    assert (xn.view(torch.int16).cpu().numpy().view(np.uint16)[:, :dim] == orc.f32_to_bf16(x32)).all()
+
+
+def test_normalize_poisson_counts(B, ctx, orc):
+    rng = synth.rng_for(3)
+    cnt = synth.poisson_counts(rng, 37, 16 * 16 * 59)
+    cnt[3, :59 * 4] = 0  # empty cells
+    x, q = B.lbp_normalize_features(ctx, dev_u16(cnt), "f32")
+    x32 = orc.normalize_f32(cnt)
+    assert (x.cpu().numpy()[:, :cnt.shape[1]].view(np.uint32) == x32.view(np.uint32)).all()
+
+
+def test_alone_equals_in_mix(B, ctx, orc):
+    g, d, r = synth.frames_with_rects(31, 4, 10, 48, 256)
+    rt = B.rects_tensor(r)
+    f_all, x_all, q_all = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), rt, x_dtype="bf16")
+    for k in [0, 7, 19, 39]:
+        f1, x1, q1 = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), rt[k:k + 1].contiguous(), x_dtype="bf16")
+        assert torch.equal(f1[0], f_all[k]) and torch.equal(x1[0], x_all[k]) and torch.equal(q1[0], q_all[k])
+
+
+# ---------------------------------------------------------------------------------------------
+# A6-A7: scoring paths against the fp64 oracle
+# ---------------------------------------------------------------------------------------------
+
+def _scoring_problem(seed, n, n_sv, C, cells=16):
+    rng = synth.rng_for(seed)
+    dim = cells * 59
+    X = synth.poisson_counts(rng, n, dim)
+    SV = synth.poisson_counts(rng, n_sv, dim)
+    a, b = synth.rbf_coefficients(rng, C, n_sv)
+    b = rng.normal(0, 0.01, C).astype(np.float32)
+    return X, SV, a, b, 1.0 / dim
+
+
+@pytest.mark.parametrize("n,n_sv,C", [(3, 300, 10), (8, 1000, 64), (300, 700, 10), (100, 3000, 64)])
+def test_rbf_f32_paths(B, ctx, orc, n, n_sv, C):
+    X, SV, a, b, gamma = _scoring_problem(n * 7 + n_sv, n, n_sv, C)
+    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype="f32")
+    x, q = B.lbp_normalize_features(ctx, dev_u16(X), "f32")
+    s, lab = B.svm_score(ctx, model, x, q)
+    x64, sv64 = orc.normalize_f64(X), orc.normalize_f64(SV)
+    ref = orc.svm_rbf(x64, sv64, a, b, gamma)
+    err = rel_score_error(s.cpu().numpy(), ref, rbf_error_scale(x64, sv64, a, b, gamma))
+    assert err <= 1e-5, err
+    agree = (lab.cpu().numpy() == orc.argmax(ref)).mean()
+    assert agree >= 0.99, agree
+
+
+@pytest.mark.parametrize("dt", ["bf16", "tf32", "fp8"])
+@pytest.mark.parametrize("n,n_sv,C", [(300, 700, 10), (100, 3000, 64), (5, 256, 16)])
+def test_rbf_tensor_core_paths(B, ctx, orc, dt, n, n_sv, C):
+    X, SV, a, b, gamma = _scoring_problem(n * 11 + n_sv, n, n_sv, C)
+    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype=dt)
+    x, q = B.lbp_normalize_features(ctx, dev_u16(X), dt, x_scale=448.0)
+    s, lab = B.svm_score(ctx, model, x, q, x_scale=448.0)
+    assert ctx.status() == 0
+    x64, sv64 = orc.normalize_f64(X), orc.normalize_f64(SV)
+    ref = orc.svm_rbf(x64, sv64, a, b, gamma)
+    err = rel_score_error(s.cpu().numpy(), ref, rbf_error_scale(x64, sv64, a, b, gamma))
+    bound = {"tf32": 2e-5, "bf16": 5e-5, "fp8": 1e-3}[dt]
+    print(f"{dt} n={n} n_sv={n_sv} C={C}: rel err {err:.3e}")
+    assert err <= bound, err
