@@ -223,6 +223,36 @@ int rgbd_svm_packed_sv(const rgbd_svm* model, const void** sv, const float** sv_
 int svm_score(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* xsq, int n,
               float x_scale, float* scores, int32_t* labels, void* stream);
 
+/* Size of the fixed scratch array behind svm_score_noalloc (16 MiB per GPU). */
+#define RGBD_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* svm_score for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of the RBF scoring above.
+ *
+ * svm_score may grow the context workspace with cudaMalloc.  Code that
+ * enqueues work while a stream is being captured into a CUDA graph, real-time
+ * loops that must not meet the device-wide synchronisation of cudaMalloc /
+ * cudaFree, and processes whose device memory is already handed out by another
+ * allocator cannot allow that.  This call allocates nothing: its partial sums
+ * live in one file-scope device array of RGBD_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits.
+ *   - Arguments and results as in svm_score.  Only RBF models packed as
+ *     RGBD_DT_BF16, RGBD_DT_FP8 or RGBD_DT_TF32 (the tensor-core path);
+ *     others give RGBD_ERR_UNSUPPORTED.
+ *   - The scratch needed grows with n x classes (4 x n x C_pad bytes per SV
+ *     split plus small terms); a call that would need more than
+ *     RGBD_NOALLOC_SCRATCH_BYTES launches nothing and returns RGBD_ERR_ARG with
+ *     the sizes in rgbd_last_error().
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, which may load the module); make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the previous
+ *     call's contents (each call overwrites what it reads).  Calls whose work
+ *     overlaps on the GPU -- on different streams, or from different threads
+ *     -- race on it and give wrong results; order them on one stream. */
+int svm_score_noalloc(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* xsq, int n,
+                      float x_scale, float* scores, int32_t* labels, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

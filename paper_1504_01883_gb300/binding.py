@@ -270,3 +270,27 @@ def svm_score(ctx, model, x, xsq=None, x_scale=448.0, scores=None, labels=None, 
     _check(lib().svm_score(ctx.handle, model.handle, _p(x), _p(xsq), n, float(x_scale), _p(scores),
                            _p(labels) if want_labels else None, _stream(stream)))
     return scores, (labels if want_labels else None)
+
+
+def svm_score_noalloc(ctx, model, x, xsq, x_scale=448.0, scores=None, labels=None, want_labels=True, stream=None):
+    """svm_score without any device allocation inside the call (see include/rgbd_lbp.h).
+
+    For callers that cannot let the library call cudaMalloc (work enqueued during CUDA-graph
+    capture, real-time loops, processes whose device memory another allocator owns): the
+    partial sums live in the library's fixed 16 MiB per-GPU scratch array.  Output tensors
+    are allocated here only when the caller does not pass them.  Calls that overlap on the GPU
+    share that array and race; keep them on one stream.
+    """
+    fn = lib().svm_score_noalloc
+    P = ctypes.c_void_p
+    fn.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_float, P, P, P]
+    fn.restype = ctypes.c_int
+    n = x.shape[0]
+    C = model.info.n_classes
+    if scores is None:
+        scores = torch.empty((n, C), dtype=torch.float32, device=x.device)
+    if want_labels and labels is None:
+        labels = torch.empty((n,), dtype=torch.int32, device=x.device)
+    _check(fn(ctx.handle, model.handle, _p(x), _p(xsq), n, float(x_scale), _p(scores),
+              _p(labels) if want_labels else None, _stream(stream)))
+    return scores, (labels if want_labels else None)

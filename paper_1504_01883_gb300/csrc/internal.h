@@ -111,6 +111,13 @@ int score_rbf_f32(rgbd_ctx* ctx, const rgbd_svm* m, const float* x, const float*
 int score_rbf_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n,
                  float x_scale, float* scores, int32_t* labels, cudaStream_t s);
 
+// Tensor-core RBF scoring with its scratch (partial sums) in a buffer the caller provides
+// instead of the context workspace.  *need receives the bytes required; when ws_bytes is
+// smaller the call launches nothing and returns RGBD_ERR_ARG.
+int score_rbf_tc_external_ws(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n,
+                             float x_scale, float* scores, int32_t* labels, cudaStream_t s, void* ws,
+                             size_t ws_bytes, size_t* need);
+
 // model packing helpers (pack.cu)
 int pack_model_tensor_maps(rgbd_svm* m);
 

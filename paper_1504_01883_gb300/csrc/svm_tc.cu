@@ -617,4 +617,94 @@ int score_rbf_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* x
                                 labels, s);
 }
 
+int score_rbf_tc_external_ws(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n,
+                             float x_scale, float* scores, int32_t* labels, cudaStream_t s, void* ws_ptr,
+                             size_t ws_cap, size_t* need) {
+    if (m->C > MAX_CPAD || !m->has_tmaps)
+        return set_error(RGBD_ERR_UNSUPPORTED, "tensor-core RBF supports up to %d classes", MAX_CPAD);
+    if (ctx->props.cc_major != 10)
+        return set_error(RGBD_ERR_UNSUPPORTED, "tensor-core path needs an sm_10x GPU");
+    int esz = 2, kind = 0;
+    uint32_t fmt = 1;  // BF16
+    CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (m->dtype == RGBD_DT_FP8) {
+        esz = 1;
+        kind = 1;
+        fmt = 0;  // E4M3
+        dt = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    } else if (m->dtype == RGBD_DT_TF32) {
+        esz = 4;
+        kind = 2;
+        fmt = 2;  // TF32
+        dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    }
+    const int mt = (n + BM - 1) / BM;
+    const int nt = m->n_pad / BN;
+    const int sms = ctx->props.sm_count;
+    int best_splits = 1;
+    long long best_cost = -1;
+    for (int sp = 1; sp <= nt; ++sp) {
+        const int tps = (nt + sp - 1) / sp;
+        const int real = (nt + tps - 1) / tps;
+        if (real != sp) continue;
+        const long long ctas = (long long)mt * sp;
+        const long long waves = (ctas + sms - 1) / sms;
+        const long long cost = waves * tps;
+        if (best_cost < 0 || cost * 100 < best_cost * 97) {
+            best_cost = cost;
+            best_splits = sp;
+        }
+    }
+    const int splits = best_splits;
+    const int tps = (nt + splits - 1) / splits;
+    const size_t part_bytes = sizeof(float) * (size_t)splits * n * m->C_pad;
+    const size_t ref_bytes = sizeof(float) * (size_t)splits * n;
+    const size_t as_bytes = sizeof(float) * (size_t)splits * m->C_pad;
+    const size_t off_ref = (part_bytes + 255) & ~size_t(255);
+    const size_t off_as = (off_ref + ref_bytes + 255) & ~size_t(255);
+    if (need) *need = off_as + as_bytes;
+    if (off_as + as_bytes > ws_cap)
+        return set_error(RGBD_ERR_ARG, "scratch of %zu bytes needed for %d rows, %d classes, %d splits; only %zu available",
+                         off_as + as_bytes, n, m->C, splits, ws_cap);
+    char* ws = (char*)ws_ptr;
+    float* part = (float*)ws;
+    float* ref = (float*)(ws + off_ref);
+    float* asplit = (float*)(ws + off_as);
+
+    CUtensorMap tm_x;
+    int rc = encode_tmap_2d(&tm_x, dt, x, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * esz, 128u / esz,
+                            BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    cudaError_t e = cudaFuncSetAttribute(rbf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return cuda_error(e, "tc smem attribute");
+    TcParams p;
+    p.n = n;
+    p.n_sv = m->n_sv;
+    p.C = m->C;
+    p.C_pad = m->C_pad;
+    p.k_blocks = m->k_pad * esz / 128;
+    p.k_elems = 128 / esz;
+    p.tiles_per_split = tps;
+    p.n_tiles = nt;
+    p.gamma = m->gamma;
+    p.gscale = (m->dtype == RGBD_DT_FP8) ? 1.0f / (x_scale * m->sv_scale) : 1.0f;
+    p.xsq = xsq;
+    p.svsq = m->sv_sq;
+    p.part = part;
+    p.ref = ref;
+    p.status = ctx->d_status;
+    p.idesc_main = make_idesc(fmt, fmt, BM, BN);
+    p.idesc_second = make_idesc(1, 1, BM, m->C_pad);
+    p.kind = kind;
+    asum_split_kernel<<<splits, 128, 0, s>>>(m->coef, m->C, m->C_pad, m->n_pad, m->n_sv, tps * BN, asplit);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "asum split launch");
+    dim3 grid(mt, splits);
+    rbf_tc_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm_x, m->tm_sv, m->tm_coef, p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "tc launch");
+    return launch_reduce_scores(part, ref, splits, n, m->C, m->C_pad, m->asum, asplit, m->bias, m->gamma, scores,
+                                labels, s);
+}
+
 }  // namespace rgbd
