@@ -95,9 +95,12 @@ struct __align__(16) Smem {
     uint32_t h1[256];                  // depth high-byte histogram
     uint32_t h2[256];                  // depth low-byte histogram inside the median's bin
     uint32_t cnt[Cfg<S>::NT];          // valid centres per half cell
+    float nvf[Cfg<S>::G * Cfg<S>::G];  // valid centres per cell (as float) ...
+    float rcp[Cfg<S>::G * Cfg<S>::G];  // ... and its IEEE reciprocal (0 for an empty cell)
     float red[Cfg<S>::NT / 32];
     int info[4];
-    uint8_t lut[256];                  // uniform-pattern bin of each code
+    uint16_t lut[257];                 // byte offset of each code's counter in a thread's histogram
+                                       // (entry 256: the unused bin 59, where invalid centres go)
 };
 
 template <int S>
@@ -118,9 +121,12 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             const bool uni = __popc(c ^ rot) <= 2;
             const unsigned m = __ballot_sync(FULL, uni);
             const int rank = prefix + __popc(m & ((1u << lane) - 1u));
-            sm.lut[c] = (uint8_t)(uni ? rank : 58);
+            const int bin = uni ? rank : 58;
+            // counters of one thread: byte (bin & 3) of word (bin / 4) * NT + thread
+            sm.lut[c] = (uint16_t)(((bin >> 2) * NT) * 4 + (bin & 3));
             prefix += __popc(m);
         }
+        if (lane == 0) sm.lut[256] = (uint16_t)(((59 >> 2) * NT) * 4 + (59 & 3));
     }
 
     const bool strict = !(a.flags & RGBD_LBP_GE);
@@ -385,7 +391,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             row3(GW, r0, gCL, gCC, gCR);
             row3(MW, r0, mCL, mCC, mCR);
             uint32_t nvalid = 0;
-            uint8_t* hb = reinterpret_cast<uint8_t*>(sm.hist);
+            uint8_t* hb_t = reinterpret_cast<uint8_t*>(sm.hist) + 4 * tid;  // this thread's counters
 #pragma unroll 2
             for (int i = 0; i < 8; ++i) {
                 row3(GW, r0 + i + 1, gDL, gDC, gDR);
@@ -401,13 +407,12 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     ((cmp_msb(gDC, gCC, cb) & (nbr_ignore ? NM : mDC)) >> 2) |
                     ((cmp_msb(gDL, gCC, cb) & (nbr_ignore ? NM : mDL)) >> 1) |
                     (cmp_msb(gCL, gCC, cb) & (nbr_ignore ? NM : mCL));
+                // branch-free: an invalid centre counts into the unused bin 59
+                nvalid += __popc(mCC);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    if ((mCC >> (8 * e + 7)) & 1u) {
-                        const int bin = sm.lut[(code >> (8 * e)) & 0xFFu];
-                        hb[((bin >> 2) * NT + tid) * 4 + (bin & 3)] += 1;
-                        ++nvalid;
-                    }
+                    const uint32_t idx = ((mCC >> (8 * e + 7)) & 1u) ? ((code >> (8 * e)) & 0xFFu) : 256u;
+                    hb_t[sm.lut[idx]] += 1;
                 }
                 gUL = gCL; gUC = gCC; gUR = gCR; gCL = gDL; gCC = gDC; gCR = gDR;
                 mUL = mCL; mUC = mCC; mUR = mCR; mCL = mDL; mCC = mDC; mCR = mDR;
@@ -420,6 +425,11 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         uint16_t* stg = reinterpret_cast<uint16_t*>(sm.img);
         {
             const int c = tid >> 1, h = tid & 1;
+            if (h == 0) {
+                const uint32_t nv = sm.cnt[2 * c] + sm.cnt[2 * c + 1];
+                sm.nvf[c] = (float)nv;
+                sm.rcp[c] = nv ? __frcp_rn((float)nv) : 0.f;
+            }
             const int w0 = h ? 8 : 0, w1 = h ? C::HW : 8;
             for (int w = w0; w < w1; ++w) {
                 const uint32_t s = sm.hist[w * NT + 2 * c] + sm.hist[w * NT + 2 * c + 1];
@@ -443,16 +453,21 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 if (a.feats) *reinterpret_cast<uint2*>(a.feats + (size_t)face * DIM + j) = hv;
             }
             if (x_dtype) {
-                float x[4];
+                // x = h / n as the IEEE single quotient: q0 = h * (1/n), then one fma correction.
+                // For 0 <= h <= n <= 64 (a cell has 64 pixels) this reproduces div.rn exactly
+                // (checked exhaustively); an empty cell has h = 0 and rcp = 0, giving 0.
+                float x[4] = {0.f, 0.f, 0.f, 0.f};
+                if (j < DIM) {  // DIM is a multiple of 4, so the whole group is inside
+                    const int c0 = j / kBins;
+                    const int split = (c0 + 1) * kBins;  // first index of the next cell
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int jj = j + e;
-                    x[e] = 0.f;
-                    if (jj < DIM) {
-                        const int cc = jj / kBins;
-                        const uint32_t nv = sm.cnt[2 * cc] + sm.cnt[2 * cc + 1];
-                        const uint32_t hc = ((e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0xFFFFu;
-                        x[e] = nv ? (float)hc / (float)nv : 0.f;
+                    for (int e = 0; e < 4; ++e) {
+                        const int cc = (j + e < split) ? c0 : c0 + 1;
+                        const float n_f = sm.nvf[cc], r_f = sm.rcp[cc];
+                        const float h_f = (float)(((e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0xFFFFu);
+                        const float q0 = __fmul_rn(h_f, r_f);
+                        const float rem = __fmaf_rn(-q0, n_f, h_f);
+                        x[e] = __fmaf_rn(rem, r_f, q0);
                     }
                 }
                 if (x_dtype == RGBD_DT_BF16) {

@@ -484,6 +484,25 @@ __global__ void asum_split_kernel(const float* __restrict__ coef, int C, int C_p
     }
 }
 
+// Number of SV-tile ranges ("splits") per 128-row block.  One CTA runs per SM, so the time
+// is about waves x (tiles per CTA + 1): the +1 stands for the pipeline fill, the epilogue of
+// the last tile and the partial-sum write that every CTA pays once.  Fewer splits win ties.
+int choose_splits(int mt, int nt, int sms) {
+    int best = 1;
+    long long best_cost = -1;
+    for (int sp = 1; sp <= nt; ++sp) {
+        const int tps = (nt + sp - 1) / sp;
+        if ((nt + tps - 1) / tps != sp) continue;
+        const long long waves = ((long long)mt * sp + sms - 1) / sms;
+        const long long cost = waves * (tps + 1);
+        if (best_cost < 0 || cost * 100 < best_cost * 97) {
+            best_cost = cost;
+            best = sp;
+        }
+    }
+    return best;
+}
+
 // Instruction descriptor of a dense tcgen05.mma: fp32 accumulator, K-major A and B.
 uint32_t make_idesc(uint32_t a_fmt, uint32_t b_fmt, int M, int N) {
     uint32_t d = 0;
@@ -544,23 +563,7 @@ int score_rbf_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* x
     }
     const int mt = (n + BM - 1) / BM;
     const int nt = m->n_pad / BN;
-    // splits: minimise (waves x tiles per CTA); prefer fewer splits on near ties
-    const int sms = ctx->props.sm_count;
-    int best_splits = 1;
-    long long best_cost = -1;
-    for (int sp = 1; sp <= nt; ++sp) {
-        const int tps = (nt + sp - 1) / sp;
-        const int real = (nt + tps - 1) / tps;
-        if (real != sp) continue;
-        const long long ctas = (long long)mt * sp;
-        const long long waves = (ctas + sms - 1) / sms;
-        const long long cost = waves * tps;
-        if (best_cost < 0 || cost * 100 < best_cost * 97) {
-            best_cost = cost;
-            best_splits = sp;
-        }
-    }
-    const int splits = best_splits;
+    const int splits = choose_splits(mt, nt, ctx->props.sm_count);
     const int tps = (nt + splits - 1) / splits;
     const size_t part_bytes = sizeof(float) * (size_t)splits * n * m->C_pad;
     const size_t ref_bytes = sizeof(float) * (size_t)splits * n;
@@ -640,22 +643,7 @@ int score_rbf_tc_external_ws(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, co
     }
     const int mt = (n + BM - 1) / BM;
     const int nt = m->n_pad / BN;
-    const int sms = ctx->props.sm_count;
-    int best_splits = 1;
-    long long best_cost = -1;
-    for (int sp = 1; sp <= nt; ++sp) {
-        const int tps = (nt + sp - 1) / sp;
-        const int real = (nt + tps - 1) / tps;
-        if (real != sp) continue;
-        const long long ctas = (long long)mt * sp;
-        const long long waves = (ctas + sms - 1) / sms;
-        const long long cost = waves * tps;
-        if (best_cost < 0 || cost * 100 < best_cost * 97) {
-            best_cost = cost;
-            best_splits = sp;
-        }
-    }
-    const int splits = best_splits;
+    const int splits = choose_splits(mt, nt, ctx->props.sm_count);
     const int tps = (nt + splits - 1) / splits;
     const size_t part_bytes = sizeof(float) * (size_t)splits * n * m->C_pad;
     const size_t ref_bytes = sizeof(float) * (size_t)splits * n;
