@@ -188,10 +188,16 @@ def main():
     ap.add_argument("--score-dtype", default="tf32", choices=["tf32", "bf16", "fp8", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-crops-per-step", type=int, default=8)
+    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision"],
+                    help="batch: the headline line; the others measure the remaining workloads")
+    ap.add_argument("--seconds", type=float, default=10.0, help="serving: simulated seconds of arrivals")
     args = ap.parse_args()
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "batch":
+        import bench_workloads
+        return bench_workloads.run(args)
 
     import torch
     import torch.distributed as dist

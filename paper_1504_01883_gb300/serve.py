@@ -1,0 +1,324 @@
+"""Continuous-batching request loop over simulated RGB-D camera streams.
+
+Frames from many cameras arrive at Poisson times.  The loop keeps the packed SVM model and a
+pool of frame slots resident on the GPU and runs, on one compute stream, batches of all faces
+of all frames that have been uploaded.  While a batch runs, frames that arrive meanwhile are
+admitted (when a slot is free and the device has memory to spare) and uploaded on a separate
+copy stream, so they form the next batch as soon as the GPU frees up: uploads overlap compute
+and batches follow each other with no gap.  Every frame's latency is measured from its arrival
+to the moment its scores and labels are on the host.
+
+``PerCropServer`` is the plain path it is compared with: each face of each frame is featurised
+and scored by its own launches, one at a time, as soon as the frame arrives.
+
+Everything on the GPU goes through the library's C ABI (``binding``); torch only provides the
+device buffers, pinned host buffers, streams and events.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import binding as B
+from . import synth
+
+
+@dataclass
+class StreamFrames:
+    """Pre-generated frames of one simulated camera (cycled through on each arrival)."""
+    grey: np.ndarray      # [P][H][W] uint8
+    depth: np.ndarray     # [P][H][W] uint16
+    rects: list           # P arrays of RECT_DTYPE (frame field = 0)
+
+
+def make_streams(seed=1508, n_streams=32, frames_per_stream=4, fmin=1, fmax=12, smin=48, smax=256,
+                 H=synth.FRAME_H, W=synth.FRAME_W):
+    rng = synth.rng_for(seed + 77)
+    out = []
+    for s in range(n_streams):
+        counts = [int(rng.integers(fmin, fmax + 1)) for _ in range(frames_per_stream)]
+        g, d, r = synth.frames_with_rects(seed * 1000 + s, frames_per_stream, counts, smin, smax, H, W)
+        per = []
+        for f in range(frames_per_stream):
+            rr = r[r["frame"] == f].copy()
+            rr["frame"] = 0
+            per.append(rr)
+        out.append(StreamFrames(g, d, per))
+    return out
+
+
+@dataclass
+class FrameRequest:
+    t_arrival: float      # seconds since the start of the run
+    stream: int
+    index: int            # arrival index within its stream (selects the pre-generated frame)
+    n_faces: int = 0
+    slot: int = -1
+    t_done: float = 0.0
+    scores: np.ndarray | None = None
+    labels: np.ndarray | None = None
+
+
+class MemoryAdmission:
+    """Admits a frame when a slot is free and the device keeps `reserve_bytes` free."""
+
+    def __init__(self, n_slots, reserve_bytes=256 << 20, mem_get_info=None):
+        self.free_slots = collections.deque(range(n_slots))
+        self.reserve = reserve_bytes
+        self.mem_get_info = mem_get_info or torch.cuda.mem_get_info
+        self.rejections = 0
+
+    def try_admit(self):
+        if not self.free_slots:
+            return -1
+        free, _ = self.mem_get_info()
+        if free < self.reserve:
+            self.rejections += 1
+            return -1
+        return self.free_slots.popleft()
+
+    def release(self, slot):
+        self.free_slots.append(slot)
+
+
+@dataclass
+class _Batch:
+    frames: list
+    done: torch.cuda.Event
+    scores_h: torch.Tensor
+    labels_h: torch.Tensor
+    n: int
+    buffer: int
+
+
+@dataclass
+class ServeReport:
+    latencies_ms: list = field(default_factory=list)
+    crops: int = 0
+    frames: int = 0
+    batches: int = 0
+    wall_s: float = 0.0
+    rejections: int = 0
+
+    def summary(self):
+        lat = np.array(self.latencies_ms) if self.latencies_ms else np.array([np.nan])
+        return {"frames": self.frames, "crops": self.crops, "batches": self.batches,
+                "crops_per_s": self.crops / self.wall_s if self.wall_s else 0.0,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(np.max(lat)), "wall_s": self.wall_s, "admission_waits": self.rejections}
+
+
+class BatchServer:
+    """Continuous batching of faces across streams (see the module docstring)."""
+
+    def __init__(self, ctx, model, streams, n_slots=96, max_faces=2048, crop=128, x_dtype="bf16",
+                 mask_mm=150, admission=None, device=None):
+        self.ctx, self.model, self.streams = ctx, model, streams
+        self.dev = device or torch.device("cuda", torch.cuda.current_device())
+        H, W = streams[0].grey.shape[1:]
+        self.H, self.W = H, W
+        self.crop, self.mask_mm = crop, mask_mm
+        self.x_dtype = B._dt(x_dtype)
+        self.max_faces = max_faces
+        self.n_slots = n_slots
+        self.grey = torch.empty((n_slots, H, W), dtype=torch.uint8, device=self.dev)
+        self.depth = torch.empty((n_slots, H, W), dtype=torch.int16, device=self.dev)
+        # pinned copies of every pre-generated frame
+        self.h_grey = [torch.from_numpy(s.grey).pin_memory() for s in streams]
+        self.h_depth = [torch.from_numpy(s.depth.view(np.int16)).pin_memory() for s in streams]
+        dim = (crop // 8) ** 2 * 59
+        self.dim = dim
+        k_pad = model.k_pad
+        C = model.info.n_classes
+        # two sets of batch buffers, so one batch can be prepared while the other runs
+        self.bufs = []
+        for _ in range(2):
+            self.bufs.append({
+                "rects_h": torch.empty((max_faces, 5), dtype=torch.int32).pin_memory(),
+                "rects": torch.empty((max_faces, 5), dtype=torch.int32, device=self.dev),
+                "x": torch.empty((max_faces, k_pad), dtype=B.x_torch_dtype(self.x_dtype), device=self.dev),
+                "xsq": torch.empty((max_faces,), dtype=torch.float32, device=self.dev),
+                "scores": torch.empty((max_faces, C), dtype=torch.float32, device=self.dev),
+                "labels": torch.empty((max_faces,), dtype=torch.int32, device=self.dev),
+                "scores_h": torch.empty((max_faces, C), dtype=torch.float32).pin_memory(),
+                "labels_h": torch.empty((max_faces,), dtype=torch.int32).pin_memory(),
+            })
+        self.compute = torch.cuda.Stream(device=self.dev)
+        self.copy = torch.cuda.Stream(device=self.dev)
+        self.admission = admission or MemoryAdmission(n_slots)
+        self.slot_ready = {}   # slot -> event recorded after its upload
+        # per-stream state kept on the device: the labels of the last served frame
+        self.last_labels = torch.full((len(streams), 12), -1, dtype=torch.int32, device=self.dev)
+
+    def _frame(self, req):
+        s = self.streams[req.stream]
+        k = req.index % len(s.rects)
+        return k, s.rects[k]
+
+    def _upload(self, req):
+        k, rects = self._frame(req)
+        req.n_faces = len(rects)
+        with torch.cuda.stream(self.copy):
+            self.grey[req.slot].copy_(self.h_grey[req.stream][k], non_blocking=True)
+            self.depth[req.slot].copy_(self.h_depth[req.stream][k], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.copy)
+        self.slot_ready[req.slot] = ev
+
+    def _launch(self, frames, buf_id):
+        buf = self.bufs[buf_id]
+        rows = []
+        for req in frames:
+            _, rects = self._frame(req)
+            for r in rects:
+                rows.append((req.slot, int(r["x"]), int(r["y"]), int(r["w"]), int(r["h"])))
+        n = len(rows)
+        buf["rects_h"][:n] = torch.tensor(rows, dtype=torch.int32)
+        cs = self.compute
+        for req in frames:
+            cs.wait_event(self.slot_ready.pop(req.slot))
+        with torch.cuda.stream(cs):
+            buf["rects"][:n].copy_(buf["rects_h"][:n], non_blocking=True)
+            rects = buf["rects"][:n]
+            B.lbp_fused_features(self.ctx, self.grey, self.depth, rects, crop=self.crop, mask_mm=self.mask_mm,
+                                 feats=False, x_dtype=self.x_dtype,
+                                 out={"x": buf["x"][:n], "xsq": buf["xsq"][:n]}, stream=cs)
+            B.svm_score(self.ctx, self.model, buf["x"][:n], buf["xsq"][:n], scores=buf["scores"][:n],
+                        labels=buf["labels"][:n], stream=cs)
+            buf["scores_h"][:n].copy_(buf["scores"][:n], non_blocking=True)
+            buf["labels_h"][:n].copy_(buf["labels"][:n], non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(cs)
+        return _Batch(frames, done, buf["scores_h"], buf["labels_h"], n, buf_id)
+
+    def _complete(self, batch, t0, report, keep_results):
+        now = time.perf_counter() - t0
+        off = 0
+        for req in batch.frames:
+            k = req.n_faces
+            if keep_results:
+                req.scores = batch.scores_h[off:off + k].numpy().copy()
+                req.labels = batch.labels_h[off:off + k].numpy().copy()
+            off += k
+            req.t_done = now
+            report.latencies_ms.append(1000.0 * (now - req.t_arrival))
+            report.frames += 1
+            report.crops += k
+            self.admission.release(req.slot)
+        report.batches += 1
+
+    def run(self, events, keep_results=False, realtime=True):
+        """events: list of (t_arrival_s, stream, n_faces) sorted by time.  Returns (report, requests)."""
+        counters = collections.Counter()
+        reqs = []
+        for t, s, _ in events:
+            reqs.append(FrameRequest(float(t), int(s), counters[s]))
+            counters[s] += 1
+        pending = collections.deque(reqs)
+        waiting = collections.deque()
+        admitted = []
+        inflight = collections.deque()
+        report = ServeReport()
+        free_bufs = [0, 1]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if not realtime:  # every frame has arrived at t = 0 (offline throughput)
+            for r in reqs:
+                r.t_arrival = 0.0
+        while pending or waiting or admitted or inflight:
+            now = time.perf_counter() - t0
+            while pending and pending[0].t_arrival <= now:
+                waiting.append(pending.popleft())
+            while waiting:
+                slot = self.admission.try_admit()
+                if slot < 0:
+                    break
+                req = waiting.popleft()
+                req.slot = slot
+                self._upload(req)
+                admitted.append(req)
+            while inflight and inflight[0].done.query():
+                b = inflight.popleft()
+                self._complete(b, t0, report, keep_results)
+                free_bufs.append(b.buffer)
+            if admitted and free_bufs and len(inflight) < 2:
+                batch, faces = [], 0
+                while admitted and faces + admitted[0].n_faces <= self.max_faces:
+                    req = admitted.pop(0)
+                    batch.append(req)
+                    faces += req.n_faces
+                inflight.append(self._launch(batch, free_bufs.pop(0)))
+                continue
+            if not (waiting or admitted) and inflight:
+                # nothing to prepare: wait for the next completion or arrival
+                nxt = pending[0].t_arrival if pending else None
+                while not inflight[0].done.query():
+                    if nxt is not None and time.perf_counter() - t0 >= nxt:
+                        break
+            elif not inflight and not waiting and not admitted and pending:
+                dt = pending[0].t_arrival - (time.perf_counter() - t0)
+                if dt > 0.0005:
+                    time.sleep(dt - 0.0003)
+        torch.cuda.synchronize()
+        report.wall_s = time.perf_counter() - t0
+        report.rejections = self.admission.rejections
+        return report, reqs
+
+
+class PerCropServer(BatchServer):
+    """The plain per-crop GPU path: each face is featurised and scored by its own launches."""
+
+    def run(self, events, keep_results=False, realtime=True):
+        counters = collections.Counter()
+        reqs = []
+        for t, s, _ in events:
+            reqs.append(FrameRequest(float(t), int(s), counters[s]))
+            counters[s] += 1
+        report = ServeReport()
+        buf = self.bufs[0]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if not realtime:
+            for r in reqs:
+                r.t_arrival = 0.0
+        cs = self.compute
+        for req in reqs:
+            dt = req.t_arrival - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            req.slot = 0
+            self._upload(req)
+            cs.wait_event(self.slot_ready.pop(0))
+            _, rects = self._frame(req)
+            k = len(rects)
+            scores = np.zeros((k, self.model.info.n_classes), np.float32)
+            labels = np.zeros(k, np.int32)
+            with torch.cuda.stream(cs):
+                for i, r in enumerate(rects):
+                    buf["rects_h"][0] = torch.tensor([0, int(r["x"]), int(r["y"]), int(r["w"]), int(r["h"])],
+                                                     dtype=torch.int32)
+                    buf["rects"][:1].copy_(buf["rects_h"][:1], non_blocking=True)
+                    B.lbp_fused_features(self.ctx, self.grey, self.depth, buf["rects"][:1], crop=self.crop,
+                                         mask_mm=self.mask_mm, feats=False, x_dtype=self.x_dtype,
+                                         out={"x": buf["x"][:1], "xsq": buf["xsq"][:1]}, stream=cs)
+                    B.svm_score(self.ctx, self.model, buf["x"][:1], buf["xsq"][:1], scores=buf["scores"][:1],
+                                labels=buf["labels"][:1], stream=cs)
+                    buf["scores_h"][:1].copy_(buf["scores"][:1], non_blocking=True)
+                    buf["labels_h"][:1].copy_(buf["labels"][:1], non_blocking=True)
+                    cs.synchronize()
+                    scores[i] = buf["scores_h"][0].numpy()
+                    labels[i] = buf["labels_h"][0].item()
+            req.n_faces = k
+            req.t_done = time.perf_counter() - t0
+            if keep_results:
+                req.scores, req.labels = scores, labels
+            report.latencies_ms.append(1000.0 * (req.t_done - req.t_arrival))
+            report.frames += 1
+            report.crops += k
+            report.batches += k
+        report.wall_s = time.perf_counter() - t0
+        return report, reqs

@@ -168,6 +168,21 @@ def poisson_counts(rng, n, dim, lam=3.0):
     return rng.poisson(lam, (n, dim)).astype(np.uint16)
 
 
+def poisson_counts_device(seed, n, dim, device, lam=3.0, chunk=4096):
+    """The same kind of rows drawn on the GPU with a seeded torch generator (for the
+    65536-row scoring workload, too large to draw on the host quickly).  Returns int16
+    storage of the uint16 counts, [n][dim]."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    out = torch.empty((n, dim), dtype=torch.int16, device=device)
+    rate = torch.full((min(chunk, n), dim), float(lam), device=device)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        out[r0:r1] = torch.poisson(rate[: r1 - r0], generator=g).to(torch.int16)
+    return out
+
+
 def rbf_coefficients(rng, n_classes, n_sv):
     """a[c][i] = alpha_ci * y_ci ~ N(0,1), shifted so each class sums to 0 (the KKT
     equality sum_i alpha_i y_i = 0 of a trained SVM); biases are 0."""
