@@ -2,20 +2,25 @@
 // function of Section 2.5, S_c = sum_i a_ci exp(-gamma |x - sv_i|^2) + b_c, for BF16, FP8 E4M3
 // (per-tensor scales) and TF32 operands with fp32 accumulation in tensor memory.
 //
-// One CTA owns 128 feature rows and a contiguous range ("split") of 128-wide SV tiles:
-//   warp 0     TMA producer: X and SV k-blocks (128 B of K per row, 128B-swizzled) into a
-//              4-stage ring; per tile the bf16 coefficient tile a[c][i] for the second MMA.
-//   warp 1     TMEM owner and MMA issuer (one thread):
-//                G[t % 2] (128 x 128 fp32, TMEM) = X . SV_t^T over all k-blocks;
-//                D (128 x C_pad fp32, TMEM)     += F_{t-1} . a_{t-1}^T   (second MMA)
-//   warps 2-5  epilogue, one thread per row: d^2 = |x|^2 + |sv|^2 - 2 G, then
-//              F = expm1(-gamma (d^2 - r)) in bf16 written to shared memory in the UMMA
-//              K-major layout, which the second MMA reads.  r is the row's mean d^2 over
-//              the split's first tile; since exp(-gamma d^2) = exp(-gamma r) (1 + F),
-//                S_c = sum_splits exp(-gamma r_s) (sum_{i in s} a_ci + D_s[c]) + b_c,
-//              and F carries the small per-SV variation with full relative precision
-//              (gamma d^2 ~ 2e-4 for gamma = 1/dim, so exp() itself is flat to 1e-4).
-// Partial sums D_s and r_s go to workspace; launch_reduce_scores combines the splits.
+// One CTA (11 warps) owns 128 feature rows and a contiguous range ("split") of 256-wide SV tiles:
+//   warp 0      TMA producer of the main ring: per k-block (128 B of K per row, 128B-swizzled)
+//               the 128-row X block and the 256-row SV block, 3 stages of 48 KB.
+//   warp 1      TMEM owner and MMA issuer (one thread):
+//                 G (128 x 256 fp32, TMEM)  = X . SV_t^T over all k-blocks   (N = 256 MMAs)
+//                 D (128 x C_pad fp32, TMEM) += F_q . a_q^T  for every 64-column chunk q of F
+//   warp 2      TMA producer of the bf16 coefficient chunks a[c][64 SVs] (2-slot ring).
+//   warps 3-10  epilogue, two sets of four warps (one per TMEM lane quarter); set k handles the
+//               64-column chunks k and k + 2 of every tile.  One thread per row reads G with
+//               tcgen05.ld, forms d^2 = |x|^2 + |sv|^2 - 2 G and F = expm1(-gamma (d^2 - r)) in
+//               bf16, and writes F into its slot of a 2-slot ring in the UMMA K-major 128B-swizzle
+//               layout, which the second MMA reads.  r is the row's mean d^2 over chunks 0
+//               and 2 of the split's first tile; since exp(-gamma d^2) = exp(-gamma r) (1 + F),
+//                 S_c = sum_splits exp(-gamma r_s) (sum_{i in s} a_ci + D_s[c]) + b_c,
+//               and F keeps the small per-SV variation at full relative precision (gamma d^2 is
+//               ~2e-4 for gamma = 1/dim, so exp() itself is flat to 1e-4).
+// The MMA thread services finished F chunks between main-loop k-blocks, so the second MMA and
+// the epilogue overlap the next tile's main loop.  Partial sums D_s and r_s go to workspace;
+// launch_reduce_scores combines the splits.
 //
 // Every wait on an mbarrier is bounded by a %globaltimer deadline; on expiry the CTA sets
 // RGBD_STATUS_WAIT_TIMEOUT, stops issuing work, waits (bounded) for its own copies and MMAs
@@ -30,31 +35,32 @@ namespace rgbd {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 128;
-constexpr int STAGES = 4;
+constexpr int BN = 256;
+constexpr int STAGES = 3;
 constexpr int X_TILE = BM * 128;   // bytes of one X k-block
 constexpr int SV_TILE = BN * 128;  // bytes of one SV k-block
 constexpr int STAGE_BYTES = X_TILE + SV_TILE;
-constexpr int F_OFF = STAGES * STAGE_BYTES;  // 2 chunks of 128 rows x 64 bf16
-constexpr int F_BYTES = BM * BN * 2;
+constexpr int F_CHUNK = BM * 64 * 2;               // one 64-column bf16 chunk of F (16 KB)
+constexpr int F_OFF = STAGES * STAGE_BYTES;        // 2 slots
 constexpr int MAX_CPAD = 128;
-constexpr int COEF_OFF = F_OFF + F_BYTES;    // 2 chunks of C_pad rows x 64 bf16
-constexpr int COEF_BYTES = MAX_CPAD * BN * 2;
-constexpr int BAR_OFF = COEF_OFF + COEF_BYTES;
-constexpr int SMEM_BYTES = BAR_OFF + 256 + 1024;  // + barriers + alignment slack
-constexpr int NUM_THREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;
-constexpr uint64_t WAIT_NS = 1000000000ull;  // 1 s: far above any legitimate wait
+constexpr int COEF_CHUNK_MAX = MAX_CPAD * 64 * 2;  // one 64-SV chunk of a (C_pad rows)
+constexpr int COEF_OFF = F_OFF + 2 * F_CHUNK;      // 2 slots
+constexpr int BAR_OFF = COEF_OFF + 2 * COEF_CHUNK_MAX;
+constexpr int SMEM_BYTES = BAR_OFF + 256 + 1024;   // + barriers + alignment slack
+constexpr int NUM_WARPS = 11;
+constexpr int NUM_THREADS = NUM_WARPS * 32;
+constexpr uint32_t TMEM_COLS = 512;                // G: 256 columns, D: C_pad columns at 256
+constexpr uint64_t WAIT_NS = 1000000000ull;        // 1 s: far above any legitimate wait
 
 // barrier slots (8 bytes each) inside the barrier block
 enum {
-    B_FULL = 0,                // STAGES
-    B_EMPTY = B_FULL + STAGES, // STAGES
-    B_GFULL = B_EMPTY + STAGES,  // 2
-    B_GEMPTY = B_GFULL + 2,      // 2
-    B_FFULL = B_GEMPTY + 2,
-    B_FEMPTY = B_FFULL + 1,
-    B_DFULL = B_FEMPTY + 1,
+    B_FULL = 0,                   // STAGES
+    B_EMPTY = B_FULL + STAGES,    // STAGES
+    B_GFULL = B_EMPTY + STAGES,
+    B_GEMPTY = B_GFULL + 1,
+    B_FFULL = B_GEMPTY + 1,       // 2 (F chunk written + its coefficient chunk loaded)
+    B_FEMPTY = B_FFULL + 2,       // 2 (second MMA of the chunk done)
+    B_DFULL = B_FEMPTY + 2,
     B_DRAIN = B_DFULL + 1,
     B_COUNT = B_DRAIN + 1
 };
@@ -163,7 +169,6 @@ __device__ __forceinline__ void mma_issue(int kind, uint32_t d, uint64_t a, uint
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
     }
 }
-
 #define TC_LD_X32(taddr, v)                                                                                   \
     asm volatile(                                                                                             \
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"     \
@@ -183,6 +188,7 @@ __device__ __forceinline__ void mma_issue(int kind, uint32_t d, uint64_t a, uint
           "=r"(v[15])                                                                                        \
         : "r"(taddr))
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 
 // ---------------------------------------------------------------------------------------
 // The kernel
@@ -204,19 +210,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int split = blockIdx.y;
     const int t0 = split * p.tiles_per_split;
     const int t1 = min(p.n_tiles, t0 + p.tiles_per_split);
-    const int U = t1 - t0;  // tiles of this split (>= 1)
+    const int U = t1 - t0;   // tiles of this split (>= 1)
+    const int Q = 4 * U;     // 64-column chunks of this split
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             bar_init(bar(B_FULL + s), 1);
             bar_init(bar(B_EMPTY + s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            bar_init(bar(B_GFULL + b), 1);
-            bar_init(bar(B_GEMPTY + b), 4);
+        bar_init(bar(B_GFULL), 1);
+        bar_init(bar(B_GEMPTY), 8);
+        for (int s = 0; s < 2; ++s) {
+            bar_init(bar(B_FFULL + s), 4 + 1);  // 4 epilogue warps + the coefficient producer
+            bar_init(bar(B_FEMPTY + s), 1);
         }
-        bar_init(bar(B_FFULL), 4 + 1);  // 4 epilogue warps + the producer's coefficient load
-        bar_init(bar(B_FEMPTY), 1);
         bar_init(bar(B_DFULL), 1);
         bar_init(bar(B_DRAIN), 1);
         *abort_flag = 0;
@@ -233,29 +240,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-
     const uint32_t coef_chunk_bytes = (uint32_t)p.C_pad * 128u;
 
     if (warp == 0) {
-        // ===================== TMA producer =====================
+        // ===================== TMA producer: X and SV k-blocks =====================
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_x) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_sv) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_coef) : "memory");
             int stage = 0;
-            uint32_t phase = 0;
-            uint32_t armed = 0;     // bit s: stage s was filled at least once
-            uint32_t armed_par = 0; // bit s: phase parity of the last fill of stage s
+            uint32_t phase = 0, armed = 0, armed_par = 0;
             bool alive = true;
-            auto load_coef = [&](int u) -> bool {
-                // coefficient tile of use u; the buffer is free once the second MMA of use u-1 is done
-                if (u >= 1 && !bar_wait(bar(B_FEMPTY), (uint32_t)((u - 1) & 1), abort_flag, p.status)) return false;
-                const int n0 = (t0 + u) * BN;
-                bar_arrive_tx(bar(B_FFULL), 2u * coef_chunk_bytes);
-                tma_load_2d(base + COEF_OFF, &tm_coef, n0, 0, bar(B_FFULL));
-                tma_load_2d(base + COEF_OFF + coef_chunk_bytes, &tm_coef, n0 + 64, 0, bar(B_FFULL));
-                return true;
-            };
             for (int u = 0; u < U && alive; ++u) {
                 const int n0 = (t0 + u) * BN;
                 for (int kb = 0; kb < p.k_blocks; ++kb) {
@@ -273,24 +267,40 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         stage = 0;
                         phase ^= 1u;
                     }
-                    // the previous tile's coefficients, once the ring is primed for this tile
-                    if (u >= 1 && kb == min(STAGES, p.k_blocks) - 1) {
-                        if (!load_coef(u - 1)) {
-                            alive = false;
-                            break;
-                        }
-                    }
                 }
             }
-            if (alive) alive = load_coef(U - 1);
-            if (!alive) {
-                // drain: wait (bounded) for the copies this thread issued
+            if (!alive) {  // drain: wait (bounded) for the copies this thread issued
                 const uint64_t tq = globaltimer();
-                for (int s = 0; s < STAGES; ++s) {
-                    if (!(armed & (1u << s))) continue;
-                    while (!bar_try(bar(B_FULL + s), (armed_par >> s) & 1u)) {
-                        if (globaltimer() - tq > WAIT_NS) break;
-                    }
+                for (int s = 0; s < STAGES; ++s)
+                    if (armed & (1u << s))
+                        while (!bar_try(bar(B_FULL + s), (armed_par >> s) & 1u) && globaltimer() - tq < WAIT_NS) {
+                        }
+            }
+        }
+    } else if (warp == 2) {
+        // ===================== TMA producer: coefficient chunks =====================
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_coef) : "memory");
+            uint32_t armed = 0, armed_par = 0;
+            bool alive = true;
+            for (int q = 0; q < Q && alive; ++q) {
+                const int slot = q & 1;
+                if (q >= 2 && !bar_wait(bar(B_FEMPTY + slot), (uint32_t)(((q - 2) >> 1) & 1), abort_flag, p.status)) {
+                    alive = false;
+                    break;
+                }
+                const int n0 = (t0 + (q >> 2)) * BN + (q & 3) * 64;
+                bar_arrive_tx(bar(B_FFULL + slot), coef_chunk_bytes);
+                tma_load_2d(base + COEF_OFF + slot * COEF_CHUNK_MAX, &tm_coef, n0, 0, bar(B_FFULL + slot));
+                armed |= 1u << slot;
+                armed_par = (armed_par & ~(1u << slot)) | ((uint32_t)((q >> 1) & 1) << slot);
+            }
+            if (!alive && armed) {
+                // the barrier cannot show these copies complete (the epilogue's arrivals are
+                // missing once aborting), so give the copies in flight a bounded 200 us to land
+                (void)armed_par;
+                const uint64_t tq = globaltimer();
+                while (globaltimer() - tq < 200000ull) {
                 }
             }
         }
@@ -300,34 +310,48 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int stage = 0;
             uint32_t phase = 0;
             bool alive = true;
+            int q_next = 0, q_avail = 0;
             const uint32_t d_tmem = tmem + 256;  // second-MMA accumulator, C_pad columns
-            auto second_mma = [&](int u) -> bool {
-                if (!bar_wait(bar(B_FFULL), (uint32_t)(u & 1), abort_flag, p.status)) return false;
+            // Issues the second MMA of the next finished F chunk; returns false if none is ready.
+            auto service = [&]() -> bool {
+                if (q_next >= q_avail) return false;
+                const int slot = q_next & 1;
+                if (!bar_try(bar(B_FFULL + slot), (uint32_t)((q_next >> 1) & 1))) return false;
                 tc_fence_after();
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t a = sdesc(base + F_OFF + c * (F_BYTES / 2) + ks * 32);
-                        const uint64_t b = sdesc(base + COEF_OFF + c * coef_chunk_bytes + ks * 32);
-                        mma_issue(0, d_tmem, a, b, p.idesc_second, (u > 0 || c > 0 || ks > 0) ? 1u : 0u);
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t a = sdesc(base + F_OFF + slot * F_CHUNK + ks * 32);
+                    const uint64_t b = sdesc(base + COEF_OFF + slot * COEF_CHUNK_MAX + ks * 32);
+                    mma_issue(0, d_tmem, a, b, p.idesc_second, (q_next > 0 || ks > 0) ? 1u : 0u);
+                }
+                tc_commit(bar(B_FEMPTY + slot));
+                ++q_next;
+                return true;
+            };
+            // Blocks (bounded) until barrier (a, parity) completes, servicing chunks meanwhile.
+            auto wait_servicing = [&](uint32_t a, uint32_t parity) -> bool {
+                const uint64_t tw = globaltimer();
+                while (!bar_try(a, parity)) {
+                    if (service()) continue;
+                    if (*abort_flag) return false;
+                    if (globaltimer() - tw > WAIT_NS) {
+                        *abort_flag = 1;
+                        atomicOr(p.status, RGBD_STATUS_WAIT_TIMEOUT);
+                        return false;
                     }
                 }
-                tc_commit(bar(B_FEMPTY));
                 return true;
             };
             for (int u = 0; u < U && alive; ++u) {
-                const int b = u & 1;
-                if (u >= 2) {
-                    if (!bar_wait(bar(B_GEMPTY + b), (uint32_t)(((u - 2) >> 1) & 1), abort_flag, p.status)) {
+                if (u >= 1) {  // the epilogue has read G of the previous tile
+                    if (!wait_servicing(bar(B_GEMPTY), (uint32_t)((u - 1) & 1))) {
                         alive = false;
                         break;
                     }
                     tc_fence_after();
                 }
-                const uint32_t g_tmem = tmem + (uint32_t)b * BN;
                 for (int kb = 0; kb < p.k_blocks; ++kb) {
-                    if (!bar_wait(bar(B_FULL + stage), phase, abort_flag, p.status)) {
+                    if (!wait_servicing(bar(B_FULL + stage), phase)) {
                         alive = false;
                         break;
                     }
@@ -337,22 +361,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     for (int ks = 0; ks < 4; ++ks) {
                         const uint64_t a = sdesc(sa + ks * 32);
                         const uint64_t bd = sdesc(sa + X_TILE + ks * 32);
-                        mma_issue(p.kind, g_tmem, a, bd, p.idesc_main, (kb > 0 || ks > 0) ? 1u : 0u);
+                        mma_issue(p.kind, tmem, a, bd, p.idesc_main, (kb > 0 || ks > 0) ? 1u : 0u);
                     }
                     tc_commit(bar(B_EMPTY + stage));
                     if (++stage == STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
+                    service();
                 }
                 if (!alive) break;
-                tc_commit(bar(B_GFULL + b));
-                if (u >= 1 && !second_mma(u - 1)) {
-                    alive = false;
-                    break;
+                tc_commit(bar(B_GFULL));
+                q_avail = 4 * (u + 1);
+            }
+            // the chunks of the last tile
+            while (alive && q_next < Q) {
+                const uint64_t tw = globaltimer();
+                while (!service()) {
+                    if (*abort_flag || globaltimer() - tw > WAIT_NS) {
+                        if (!*abort_flag) atomicOr(p.status, RGBD_STATUS_WAIT_TIMEOUT);
+                        *abort_flag = 1;
+                        alive = false;
+                        break;
+                    }
                 }
             }
-            if (alive) alive = second_mma(U - 1);
             if (alive) tc_commit(bar(B_DFULL));
             // drain: every MMA this thread issued has completed once B_DRAIN flips
             tc_commit(bar(B_DRAIN));
@@ -362,8 +395,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
         }
     } else {
-        // ===================== epilogue: warps 2..5, one thread per row =====================
-        const int quarter = warp & 3;  // TMEM lanes this warp may access
+        // ===================== epilogue: warps 3..10, one thread per row =====================
+        const int ew = warp - 3;           // 0..7
+        const int set = ew >> 2;           // chunks set, set + 2 of every tile
+        const int quarter = warp & 3;      // TMEM lanes this warp may access
         const int row = quarter * 32 + lane;
         const int grow = m0 + row;
         const bool row_ok = grow < p.n;
@@ -377,74 +412,79 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             return __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
         };
         for (int u = 0; u < U && alive; ++u) {
-            const int b = u & 1;
             const int n0 = (t0 + u) * BN;
-            if (!wait_warp(bar(B_GFULL + b), (uint32_t)((u >> 1) & 1))) {
+            if (!wait_warp(bar(B_GFULL), (uint32_t)(u & 1))) {
                 alive = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t g_tmem = tmem + lane_addr + (uint32_t)b * BN;
-            const int valid_cols = min(BN, p.n_sv - n0);
+            const uint32_t g_tmem = tmem + lane_addr;
             if (u == 0) {
+                // reference distance: mean d^2 over the valid columns of chunks 0 and 2 of the
+                // split's first tile; both warp sets compute the same value independently
                 float sum = 0.f;
+                int cnt = 0;
 #pragma unroll 1
-                for (int ch = 0; ch < 4; ++ch) {
-                    uint32_t v[32];
-                    TC_LD_X32(g_tmem + ch * 32, v);
-                    tc_wait_ld();
+                for (int h = 0; h < 2; ++h) {
+                    const int c = 2 * h;
+#pragma unroll 1
+                    for (int half = 0; half < 2; ++half) {
+                        uint32_t v[32];
+                        TC_LD_X32(g_tmem + c * 64 + half * 32, v);
+                        tc_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = ch * 32 + j;
-                        if (col < valid_cols) {
-                            const float d2 = xs + __ldg(p.svsq + n0 + col) - 2.f * p.gscale * __uint_as_float(v[j]);
-                            sum += d2;
+                        for (int j = 0; j < 32; ++j) {
+                            const int col = c * 64 + half * 32 + j;
+                            if (n0 + col < p.n_sv) {
+                                sum += xs + __ldg(p.svsq + n0 + col) - 2.f * p.gscale * __uint_as_float(v[j]);
+                                ++cnt;
+                            }
                         }
                     }
                 }
-                r = sum / (float)max(valid_cols, 1);
+                r = sum / (float)max(cnt, 1);
             }
-            // the F / coefficient buffer is free once the second MMA of the previous tile is done
-            if (u >= 1 && !wait_warp(bar(B_FEMPTY), (uint32_t)((u - 1) & 1))) {
-                alive = false;
-                break;
-            }
-            unsigned char* fb = gbase + F_OFF;
 #pragma unroll 1
-            for (int ch = 0; ch < 4; ++ch) {
-                uint32_t v[32];
-                TC_LD_X32(g_tmem + ch * 32, v);
-                tc_wait_ld();
-                uint32_t pk[16];
+            for (int h = 0; h < 2; ++h) {
+                const int c = set + 2 * h;  // chunk within the tile
+                const int q = 4 * u + c;    // chunk index within the split
+                uint32_t pk[32];
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
-                    const int col = ch * 32 + j;
-                    const float d0 = xs + __ldg(p.svsq + n0 + col) - 2.f * p.gscale * __uint_as_float(v[j]);
-                    const float d1 = xs + __ldg(p.svsq + n0 + col + 1) - 2.f * p.gscale * __uint_as_float(v[j + 1]);
-                    const float f0 = expm1f(-p.gamma * (d0 - r));
-                    const float f1 = expm1f(-p.gamma * (d1 - r));
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
-                    pk[j >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+                for (int half = 0; half < 2; ++half) {
+                    uint32_t v[32];
+                    TC_LD_X32(g_tmem + c * 64 + half * 32, v);
+                    tc_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        const int col = n0 + c * 64 + half * 32 + j;
+                        const float d0 = xs + __ldg(p.svsq + col) - 2.f * p.gscale * __uint_as_float(v[j]);
+                        const float d1 = xs + __ldg(p.svsq + col + 1) - 2.f * p.gscale * __uint_as_float(v[j + 1]);
+                        const __nv_bfloat162 hv = __floats2bfloat162_rn(expm1f(-p.gamma * (d0 - r)),
+                                                                        expm1f(-p.gamma * (d1 - r)));
+                        pk[half * 16 + (j >> 1)] = *reinterpret_cast<const uint32_t*>(&hv);
+                    }
                 }
-                // 32 columns = 4 granules of 16 B inside 64-column chunk ch / 2
-                const int c = ch >> 1;
-                unsigned char* rowp = fb + c * (F_BYTES / 2) + (row >> 3) * 1024 + (row & 7) * 128;
+                if (h == 1) {  // this set's last read of G for the tile
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(bar(B_GEMPTY));
+                }
+                // the slot is free once the second MMA of chunk q - 2 is done
+                if (q >= 2 && !wait_warp(bar(B_FEMPTY + set), (uint32_t)(((q - 2) >> 1) & 1))) {
+                    alive = false;
+                    break;
+                }
+                unsigned char* rowp = gbase + F_OFF + set * F_CHUNK + (row >> 3) * 1024 + (row & 7) * 128;
 #pragma unroll
-                for (int g4 = 0; g4 < 4; ++g4) {
-                    const int g = (ch & 1) * 4 + g4;
+                for (int g = 0; g < 8; ++g)
                     *reinterpret_cast<uint4*>(rowp + ((g ^ (row & 7)) << 4)) =
-                        make_uint4(pk[4 * g4], pk[4 * g4 + 1], pk[4 * g4 + 2], pk[4 * g4 + 3]);
-                }
-            }
-            tc_fence_before();
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) {
-                bar_arrive(bar(B_GEMPTY + b));
-                bar_arrive(bar(B_FFULL));
+                        make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) bar_arrive(bar(B_FFULL + set));
             }
         }
-        if (alive && wait_warp(bar(B_DFULL), 0)) {
+        if (alive && set == 0 && wait_warp(bar(B_DFULL), 0)) {
             tc_fence_after();
             const uint32_t d_tmem = tmem + lane_addr + 256;
             float* prow = p.part + ((size_t)split * p.n + grow) * p.C_pad;
@@ -541,63 +581,68 @@ int pack_model_tensor_maps(rgbd_svm* m) {
     return RGBD_OK;
 }
 
-int score_rbf_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n, float x_scale,
-                 float* scores, int32_t* labels, cudaStream_t s) {
+namespace {
+
+struct TcPlan {
+    int esz, kind, splits, tps, mt, nt;
+    uint32_t fmt;
+    CUtensorMapDataType dt;
+    size_t off_ref, off_as, bytes;
+};
+
+int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
     if (m->C > MAX_CPAD || !m->has_tmaps)
         return set_error(RGBD_ERR_UNSUPPORTED, "svm_score: tensor-core RBF supports up to %d classes", MAX_CPAD);
     if (ctx->props.cc_major != 10)
         return set_error(RGBD_ERR_UNSUPPORTED, "svm_score: tensor-core path needs an sm_10x GPU");
-    int esz = 2, kind = 0;
-    uint32_t fmt = 1;  // BF16
-    CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    pl->esz = 2;
+    pl->kind = 0;
+    pl->fmt = 1;  // BF16
+    pl->dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     if (m->dtype == RGBD_DT_FP8) {
-        esz = 1;
-        kind = 1;
-        fmt = 0;  // E4M3
-        dt = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+        pl->esz = 1;
+        pl->kind = 1;
+        pl->fmt = 0;  // E4M3
+        pl->dt = CU_TENSOR_MAP_DATA_TYPE_UINT8;
     } else if (m->dtype == RGBD_DT_TF32) {
-        esz = 4;
-        kind = 2;
-        fmt = 2;  // TF32
-        dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        pl->esz = 4;
+        pl->kind = 2;
+        pl->fmt = 2;  // TF32
+        pl->dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     }
-    const int mt = (n + BM - 1) / BM;
-    const int nt = m->n_pad / BN;
-    const int splits = choose_splits(mt, nt, ctx->props.sm_count);
-    const int tps = (nt + splits - 1) / splits;
-    const size_t part_bytes = sizeof(float) * (size_t)splits * n * m->C_pad;
-    const size_t ref_bytes = sizeof(float) * (size_t)splits * n;
-    const size_t as_bytes = sizeof(float) * (size_t)splits * m->C_pad;
-    const size_t off_ref = (part_bytes + 255) & ~size_t(255);
-    const size_t off_as = (off_ref + ref_bytes + 255) & ~size_t(255);
-    int rc = ensure_workspace(ctx, off_as + as_bytes, s);
-    if (rc) return rc;
-    char* ws = (char*)ctx->workspace;
+    pl->mt = (n + BM - 1) / BM;
+    pl->nt = m->n_pad / BN;
+    pl->splits = choose_splits(pl->mt, pl->nt, ctx->props.sm_count);
+    pl->tps = (pl->nt + pl->splits - 1) / pl->splits;
+    const size_t part_bytes = sizeof(float) * (size_t)pl->splits * n * m->C_pad;
+    const size_t ref_bytes = sizeof(float) * (size_t)pl->splits * n;
+    const size_t as_bytes = sizeof(float) * (size_t)pl->splits * m->C_pad;
+    pl->off_ref = (part_bytes + 255) & ~size_t(255);
+    pl->off_as = (pl->off_ref + ref_bytes + 255) & ~size_t(255);
+    pl->bytes = pl->off_as + as_bytes;
+    return RGBD_OK;
+}
+
+int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n, float x_scale,
+              float* scores, int32_t* labels, cudaStream_t s, const TcPlan& pl, char* ws) {
     float* part = (float*)ws;
-    float* ref = (float*)(ws + off_ref);
-    float* asplit = (float*)(ws + off_as);
-
+    float* ref = (float*)(ws + pl.off_ref);
+    float* asplit = (float*)(ws + pl.off_as);
     CUtensorMap tm_x;
-    rc = encode_tmap_2d(&tm_x, dt, x, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * esz, 128u / esz, BM,
-                        CU_TENSOR_MAP_SWIZZLE_128B);
+    int rc = encode_tmap_2d(&tm_x, pl.dt, x, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * pl.esz,
+                            128u / pl.esz, BM, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
-
-    static bool attr_set = false;
-    cudaError_t e;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(rbf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return cuda_error(e, "svm_score: tc smem attribute");
-        attr_set = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(rbf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return cuda_error(e, "svm_score: tc smem attribute");
     TcParams p;
     p.n = n;
     p.n_sv = m->n_sv;
     p.C = m->C;
     p.C_pad = m->C_pad;
-    p.k_blocks = m->k_pad * esz / 128;
-    p.k_elems = 128 / esz;
-    p.tiles_per_split = tps;
-    p.n_tiles = nt;
+    p.k_blocks = m->k_pad * pl.esz / 128;
+    p.k_elems = 128 / pl.esz;
+    p.tiles_per_split = pl.tps;
+    p.n_tiles = pl.nt;
     p.gamma = m->gamma;
     p.gscale = (m->dtype == RGBD_DT_FP8) ? 1.0f / (x_scale * m->sv_scale) : 1.0f;
     p.xsq = xsq;
@@ -605,94 +650,43 @@ int score_rbf_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* x
     p.part = part;
     p.ref = ref;
     p.status = ctx->d_status;
-    p.idesc_main = make_idesc(fmt, fmt, BM, BN);
+    p.idesc_main = make_idesc(pl.fmt, pl.fmt, BM, BN);
     p.idesc_second = make_idesc(1, 1, BM, m->C_pad);
-    p.kind = kind;
-
-    asum_split_kernel<<<splits, 128, 0, s>>>(m->coef, m->C, m->C_pad, m->n_pad, m->n_sv, tps * BN, asplit);
+    p.kind = pl.kind;
+    asum_split_kernel<<<pl.splits, 128, 0, s>>>(m->coef, m->C, m->C_pad, m->n_pad, m->n_sv, pl.tps * BN, asplit);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "svm_score: asum split launch");
-    dim3 grid(mt, splits);
+    dim3 grid(pl.mt, pl.splits);
     rbf_tc_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm_x, m->tm_sv, m->tm_coef, p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "svm_score: tc launch");
-    return launch_reduce_scores(part, ref, splits, n, m->C, m->C_pad, m->asum, asplit, m->bias, m->gamma, scores,
+    return launch_reduce_scores(part, ref, pl.splits, n, m->C, m->C_pad, m->asum, asplit, m->bias, m->gamma, scores,
                                 labels, s);
+}
+
+}  // namespace
+
+int score_rbf_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n, float x_scale,
+                 float* scores, int32_t* labels, cudaStream_t s) {
+    TcPlan pl;
+    int rc = plan_tc(ctx, m, n, &pl);
+    if (rc) return rc;
+    rc = ensure_workspace(ctx, pl.bytes, s);
+    if (rc) return rc;
+    return launch_tc(ctx, m, x, xsq, n, x_scale, scores, labels, s, pl, (char*)ctx->workspace);
 }
 
 int score_rbf_tc_external_ws(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n,
                              float x_scale, float* scores, int32_t* labels, cudaStream_t s, void* ws_ptr,
                              size_t ws_cap, size_t* need) {
-    if (m->C > MAX_CPAD || !m->has_tmaps)
-        return set_error(RGBD_ERR_UNSUPPORTED, "tensor-core RBF supports up to %d classes", MAX_CPAD);
-    if (ctx->props.cc_major != 10)
-        return set_error(RGBD_ERR_UNSUPPORTED, "tensor-core path needs an sm_10x GPU");
-    int esz = 2, kind = 0;
-    uint32_t fmt = 1;  // BF16
-    CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    if (m->dtype == RGBD_DT_FP8) {
-        esz = 1;
-        kind = 1;
-        fmt = 0;  // E4M3
-        dt = CU_TENSOR_MAP_DATA_TYPE_UINT8;
-    } else if (m->dtype == RGBD_DT_TF32) {
-        esz = 4;
-        kind = 2;
-        fmt = 2;  // TF32
-        dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    }
-    const int mt = (n + BM - 1) / BM;
-    const int nt = m->n_pad / BN;
-    const int splits = choose_splits(mt, nt, ctx->props.sm_count);
-    const int tps = (nt + splits - 1) / splits;
-    const size_t part_bytes = sizeof(float) * (size_t)splits * n * m->C_pad;
-    const size_t ref_bytes = sizeof(float) * (size_t)splits * n;
-    const size_t as_bytes = sizeof(float) * (size_t)splits * m->C_pad;
-    const size_t off_ref = (part_bytes + 255) & ~size_t(255);
-    const size_t off_as = (off_ref + ref_bytes + 255) & ~size_t(255);
-    if (need) *need = off_as + as_bytes;
-    if (off_as + as_bytes > ws_cap)
-        return set_error(RGBD_ERR_ARG, "scratch of %zu bytes needed for %d rows, %d classes, %d splits; only %zu available",
-                         off_as + as_bytes, n, m->C, splits, ws_cap);
-    char* ws = (char*)ws_ptr;
-    float* part = (float*)ws;
-    float* ref = (float*)(ws + off_ref);
-    float* asplit = (float*)(ws + off_as);
-
-    CUtensorMap tm_x;
-    int rc = encode_tmap_2d(&tm_x, dt, x, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * esz, 128u / esz,
-                            BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    TcPlan pl;
+    int rc = plan_tc(ctx, m, n, &pl);
     if (rc) return rc;
-    cudaError_t e = cudaFuncSetAttribute(rbf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return cuda_error(e, "tc smem attribute");
-    TcParams p;
-    p.n = n;
-    p.n_sv = m->n_sv;
-    p.C = m->C;
-    p.C_pad = m->C_pad;
-    p.k_blocks = m->k_pad * esz / 128;
-    p.k_elems = 128 / esz;
-    p.tiles_per_split = tps;
-    p.n_tiles = nt;
-    p.gamma = m->gamma;
-    p.gscale = (m->dtype == RGBD_DT_FP8) ? 1.0f / (x_scale * m->sv_scale) : 1.0f;
-    p.xsq = xsq;
-    p.svsq = m->sv_sq;
-    p.part = part;
-    p.ref = ref;
-    p.status = ctx->d_status;
-    p.idesc_main = make_idesc(fmt, fmt, BM, BN);
-    p.idesc_second = make_idesc(1, 1, BM, m->C_pad);
-    p.kind = kind;
-    asum_split_kernel<<<splits, 128, 0, s>>>(m->coef, m->C, m->C_pad, m->n_pad, m->n_sv, tps * BN, asplit);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "asum split launch");
-    dim3 grid(mt, splits);
-    rbf_tc_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm_x, m->tm_sv, m->tm_coef, p);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "tc launch");
-    return launch_reduce_scores(part, ref, splits, n, m->C, m->C_pad, m->asum, asplit, m->bias, m->gamma, scores,
-                                labels, s);
+    if (need) *need = pl.bytes;
+    if (pl.bytes > ws_cap)
+        return set_error(RGBD_ERR_ARG, "scratch of %zu bytes needed for %d rows, %d classes, %d splits; only %zu available",
+                         pl.bytes, n, m->C, pl.splits, ws_cap);
+    return launch_tc(ctx, m, x, xsq, n, x_scale, scores, labels, s, pl, (char*)ws_ptr);
 }
 
 }  // namespace rgbd
