@@ -90,7 +90,7 @@ template <int S>
 struct __align__(16) Smem {
     uint32_t img[2 * S * S / 4];       // grey words, then mask words; later the uint16 staging row
     uint32_t hist[Cfg<S>::HW * Cfg<S>::NT];  // thread-private 8-bit counts, word (bin/4)*NT + t
-    uint2 colmap[S];                   // taps per crop column, index (u % 4) * SW + u / 4
+    uint2 colmap[S];                   // taps per crop column, read two at a time (uint4)
     uint2 rowmap[S];                   // taps per crop row
     uint32_t h1[256];                  // depth high-byte histogram
     uint32_t h2[256];                  // depth low-byte histogram inside the median's bin
@@ -156,7 +156,9 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             } else if (ok) {
                 for (int i = tid; i < 2 * S; i += NT) {
                     if (i < S) {
-                        sm.colmap[(i & 3) * SW + (i >> 2)] = make_tap(rect_coord_q16(r.x, r.w, S, i), a.W);
+                        // column u = 4q + e lives at uint2 index ((e / 2) * SW + q) * 2 + e % 2
+                        sm.colmap[(((i & 3) >> 1) * SW + (i >> 2)) * 2 + (i & 1)] =
+                            make_tap(rect_coord_q16(r.x, r.w, S, i), a.W);
                     } else {
                         const int v = i - S;
                         sm.rowmap[v] = make_tap(rect_coord_q16(r.y, r.h, S, v), a.H);
@@ -176,6 +178,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         __syncthreads();
 
         // ---- P1: resample; grey to shared memory, depth to registers ----------------------
+        // All taps are gathered first (independent loads, no warp-synchronous step in
+        // between), then the high-byte histogram of the non-zero depths is built.
         uint32_t dreg[16];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -190,13 +194,30 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     d23 = dd.y;
                 } else if (!a.affine) {
                     const uint2 rm = sm.rowmap[v];
+                    const uint32_t fy = rm.x >> 24;
+                    const uint8_t* g0 = gsrc + (size_t)(rm.x & 0xFFFFu) * a.W;
+                    const uint8_t* g1 = g0 + (size_t)((rm.x >> 16) & 1u) * a.W;
                     const uint16_t* drow = dsrc + (size_t)rm.y * a.W;
+                    const uint4* cm4 = reinterpret_cast<const uint4*>(sm.colmap);
                     uint32_t dv[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const uint2 cm = sm.colmap[e * SW + q];
-                        gw |= bilerp(gsrc, a.W, cm.x, rm.x) << (8 * e);
-                        dv[e] = __ldg(drow + cm.y);
+                    for (int e2 = 0; e2 < 2; ++e2) {
+                        const uint4 cc = cm4[e2 * SW + q];  // taps of columns 4q + 2 e2 and + 1
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const uint32_t cx = j ? cc.z : cc.x;
+                            const uint32_t xa = cx & 0xFFFFu, dx = (cx >> 16) & 1u;
+                            const int fx = (int)(cx >> 24);
+                            const int p00 = __ldg(g0 + xa), p01 = __ldg(g0 + xa + dx);
+                            const int p10 = __ldg(g1 + xa), p11 = __ldg(g1 + xa + dx);
+                            // (256 - f) a + f b = 256 a + f (b - a), exactly
+                            const int h0 = (p00 << 8) + fx * (p01 - p00);
+                            const int h1 = (p10 << 8) + fx * (p11 - p10);
+                            const int acc = (h0 << 8) + (int)fy * (h1 - h0);
+                            const int e = 2 * e2 + j;
+                            gw |= (uint32_t)((acc + 32768) >> 16) << (8 * e);
+                            dv[e] = __ldg(drow + (j ? cc.w : cc.y));
+                        }
                     }
                     d01 = dv[0] | (dv[1] << 16);
                     d23 = dv[2] | (dv[3] << 16);
@@ -218,8 +239,12 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             sm.img[item] = gw;
             dreg[2 * k] = d01;
             dreg[2 * k + 1] = d23;
-
-            // high-byte histogram of the non-zero depths
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            // high-byte histogram of the non-zero depths, warp-aggregated when a warp's values
+            // fall in at most two neighbouring bins
+            const uint32_t d01 = dreg[2 * k], d23 = dreg[2 * k + 1];
             const uint32_t dv4[4] = {d01 & 0xFFFFu, d01 >> 16, d23 & 0xFFFFu, d23 >> 16};
             int kmin = 256, kmax = -1;
 #pragma unroll
