@@ -248,6 +248,12 @@ def main():
         stage2()
     torch.cuda.synchronize()
     ctx.status(clear=True)
+    # launch layout chosen by the project's autotuner (untimed; nothing is cached across runs here)
+    from paper_1504_01883_gb300 import autotune
+    tuning, tune_report = autotune.tune(ctx, f"batch-{n}x{dim}-sv{wl.sv_counts.shape[0]}-c{wl.coef.shape[0]}-{dt}",
+                                        stage1, stage2, n, wl.sv_counts.shape[0], stream, use_cache=False,
+                                        tensor_core=(dt != "f32"))
+    torch.cuda.synchronize()
 
     g1, g2 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
     with torch.cuda.graph(g1, stream=stream):
@@ -290,13 +296,11 @@ def main():
     t_step = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)]
     t_k1 = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
     t_k2 = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
-    total_ms = float(np.sum(t_step))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    from paper_1504_01883_gb300 import replicas
+    my_ms = float(np.sum(t_step))
+    total_ms = replicas.max_over_ranks(my_ms, dev)  # slowest rank
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms / 1000.0)
+    value = replicas.job_throughput(n * args.steps, total_ms / 1000.0, dev)  # all ranks' faces
     status = ctx.status(clear=True)
 
     # ---- end to end through the same calls, from pinned host memory --------------------------
@@ -355,7 +359,8 @@ def main():
             "roofline": roofline, "stages": {"k1": rl_k1, "k2": rl_k2},
             "e2e": {"value": round(world * n / (e2e_ms * 1e-3), 1), "unit": "crops/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
-            "gpu_launches": launches_per_step * args.steps, "clocks": clk, "device_status": status}
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk, "device_status": status,
+            "autotune": {"tuning": tune_report["tuning"], "timed_ms": tune_report["report"]}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:

@@ -62,6 +62,8 @@ extern "C" {
 /* ---- LBP option flags ------------------------------------------------------------------- */
 #define RGBD_LBP_GE 0x1               /* s(g_p - g_c) = [g_p >= g_c] instead of [g_p > g_c] */
 #define RGBD_LBP_NBR_IGNORE_MASK 0x2  /* neighbours compare on grey whatever their depth */
+#define RGBD_LBP_FACE_HIST256 0x4     /* one 0-255 histogram of the raw codes per face (Section 3's
+                                         form): cell must equal crop, crop 8..255, dim = 256 */
 
 /* A face rectangle on frame `frame`: top-left (x, y), width w, height h, in
  * frame pixels.  It may extend past the frame border (taps are clamped). */
@@ -113,6 +115,18 @@ int rgbd_ctx_reserve(rgbd_ctx* ctx, size_t bytes);
 /* Reads the device status word (synchronises the device).  flags (host) may be
  * NULL; with clear != 0 the word is reset to 0 afterwards. */
 int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear);
+
+/* Launch-shape knobs of a context, set by an autotuner (0 restores the built-in choice).
+ * They change only how work is laid out on the GPU, never a result bit of the integer
+ * path; scores change within rounding (the split of the SV sum).
+ *   RGBD_TUNE_LBP_CTAS_PER_SM   resident fused-kernel CTAs per SM (1 or 2)
+ *   RGBD_TUNE_TC_SPLITS         SV-tile ranges per 128-row block in tensor-core scoring
+ *   RGBD_TUNE_TC_MULTICAST      1 = CTA pairs share SV tiles by TMA multicast, 2 = off
+ * Errors: RGBD_ERR_ARG for an unknown key or a negative value. */
+#define RGBD_TUNE_LBP_CTAS_PER_SM 1
+#define RGBD_TUNE_TC_SPLITS 2
+#define RGBD_TUNE_TC_MULTICAST 3
+int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value);
 
 /* ======================================================================================= */
 /* A1: affine crop (Section 2.1, Eq. 1 p' = x.u + y.v + t; Section 3: each face is      */
@@ -172,6 +186,11 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
                        int crop, int cell, int mask_mm, int flags, uint16_t* feats, int x_dtype,
                        void* x_out, int k_pad, float x_scale, float* xsq_out, void* stream);
 
+/* With flags & RGBD_LBP_FACE_HIST256 the same call computes the paper's own face descriptor
+ * (Section 3: after the LBP codes, "histogram is calculated ranging from 0 to 255, for each
+ * face"): crop any size 8..255 (the paper resizes faces to 200x200), cell == crop, and feats
+ * is uint16 [n][256], bin = raw code.  Mask, codes and normalisation are as above (one cell). */
+
 /* A5 alone: per-cell normalisation of count rows that came from elsewhere (a
  * stored database, synthetic counts).  feats uint16 [n][dim], dim a multiple
  * of nbins; other arguments as in lbp_fused_features. */
@@ -222,6 +241,22 @@ int rgbd_svm_packed_sv(const rgbd_svm* model, const void** sv, const float** sv_
  * Errors: RGBD_ERR_ARG, RGBD_ERR_UNSUPPORTED, RGBD_ERR_NOMEM, RGBD_ERR_CUDA. */
 int svm_score(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* xsq, int n,
               float x_scale, float* scores, int32_t* labels, void* stream);
+
+/* ======================================================================================= */
+/* Nearest-centre face tracking (Section 2.3)                                              */
+/* ======================================================================================= */
+
+/* For each face of the previous frame, the face of the current frame whose rect centre is
+ * nearest to its own (Section 2.3: person A's face in the next frame is the detected face
+ * whose centre is nearest to A's previous centre).  The `frame` field of each rect is the
+ * camera stream id: faces only match faces of the same stream.
+ *   prev  rgbd_rect [n_prev], cur rgbd_rect [n_cur] (device)
+ *   match int32 [n_prev] (device): index into cur, or -1 when the stream has no current
+ *         face.  Centres are compared exactly as (2x + w, 2y + h); ties go to the lowest index.
+ * Each previous face is matched independently (two may pick the same current face).
+ * Errors: RGBD_ERR_ARG. */
+int rgbd_track_nearest(rgbd_ctx* ctx, const rgbd_rect* prev, int n_prev, const rgbd_rect* cur, int n_cur,
+                       int32_t* match, void* stream);
 
 /* Size of the fixed scratch array behind svm_score_noalloc (16 MiB per GPU). */
 #define RGBD_NOALLOC_SCRATCH_BYTES (16u << 20)

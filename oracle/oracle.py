@@ -21,7 +21,7 @@ __all__ = [
     "build", "lib", "rect_coord_q16", "crop", "median_nonzero", "valid_mask", "lbp_code",
     "lbp_codes", "uniform_table", "histograms", "features_batch", "normalize_f64",
     "normalize_f32", "f32_to_bf16", "f32_to_e4m3", "e4m3_to_f64", "svm_rbf", "svm_linear",
-    "argmax", "RECT_DTYPE", "LBP_GE", "LBP_NBR_IGNORE_MASK",
+    "argmax", "track_nearest", "RECT_DTYPE", "LBP_GE", "LBP_NBR_IGNORE_MASK",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -266,4 +266,17 @@ def argmax(scores):
     n, C = scores.shape
     out = np.zeros(n, np.int32)
     lib().orc_argmax(_p(scores), n, C, _p(out))
+    return out
+
+
+# ---- Section 2.3: nearest-centre tracking ---------------------------------------------------
+
+def track_nearest(prev, cur):
+    """For each previous rect, the index of the nearest current rect of the same stream, or -1."""
+    prev = np.ascontiguousarray(prev, RECT_DTYPE)
+    cur = np.ascontiguousarray(cur, RECT_DTYPE)
+    L = lib()
+    L.orc_track_nearest.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    out = np.zeros(len(prev), np.int32)
+    L.orc_track_nearest(_p(prev), len(prev), _p(cur), len(cur), _p(out))
     return out

@@ -380,3 +380,29 @@ void orc_argmax(const double* scores, int n, int n_classes, int32_t* labels) {
         labels[k] = best;
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Section 2.3: nearest-centre tracking.                               */
+/* ------------------------------------------------------------------ */
+
+/* For each previous face, the index of the current face (same stream id in `frame`) whose
+ * rect centre (x + w/2, y + h/2) is nearest in Euclidean distance; -1 if the stream has no
+ * current face; ties go to the lowest index.  Distances are compared in fp64 on the
+ * half-pixel centres. */
+void orc_track_nearest(const orc_rect* prev, int n_prev, const orc_rect* cur, int n_cur, int32_t* match) {
+    for (int i = 0; i < n_prev; ++i) {
+        double px = prev[i].x + prev[i].w / 2.0, py = prev[i].y + prev[i].h / 2.0;
+        int best = -1;
+        double bd = 0.0;
+        for (int j = 0; j < n_cur; ++j) {
+            if (cur[j].frame != prev[i].frame) continue;
+            double cx = cur[j].x + cur[j].w / 2.0, cy = cur[j].y + cur[j].h / 2.0;
+            double d = sqrt((cx - px) * (cx - px) + (cy - py) * (cy - py));
+            if (best < 0 || d < bd) {
+                best = j;
+                bd = d;
+            }
+        }
+        match[i] = best;
+    }
+}

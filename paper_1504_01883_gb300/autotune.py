@@ -1,0 +1,126 @@
+"""Autotuner of the launch layout.
+
+It times the two stages of a workload (the fused feature kernel and the scoring kernels) under
+candidate settings of the context's tuning knobs and keeps the fastest:
+
+  K1  resident fused-kernel CTAs per SM (1 or 2): one 512-thread CTA per face works on a
+      128 x 128 crop laid out as 16 x 16 cells of 8 x 8 pixels, two half-cell column tiles per
+      cell, so this picks between one or two such crop tiles in flight per SM;
+  K2  how many SV-tile ranges ("splits") each 128-row block of the tensor-core scoring
+      kernel is cut into (the row x SV tiling across SMs), and whether CTA pairs share SV
+      tiles by TMA multicast.
+
+Choices never change the integer features, only the order of the SV sum (scores move within
+rounding).  Results are cached in a JSON file keyed by GPU name and workload shape.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+from dataclasses import asdict, dataclass
+
+import torch
+
+from . import binding as B
+
+CACHE_PATH = os.environ.get("RGBD_TUNE_CACHE",
+                            os.path.join(os.path.expanduser("~"), ".cache", "rgbd_lbp_gb300", "tune.json"))
+
+
+@dataclass
+class Tuning:
+    lbp_ctas_per_sm: int = 0
+    tc_splits: int = 0
+    tc_multicast: int = 0
+
+    def apply(self, ctx):
+        ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, self.lbp_ctas_per_sm)
+        ctx.set_tuning(B.TUNE_TC_SPLITS, self.tc_splits)
+        ctx.set_tuning(B.TUNE_TC_MULTICAST, self.tc_multicast)
+
+
+def _time(fn, stream, reps=3):
+    ts = []
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts[1:])
+
+
+def split_candidates(n_rows, n_sv, sms=152):
+    """Split counts worth timing: the cost model's neighbourhood of whole-wave layouts."""
+    mt = (n_rows + 127) // 128
+    nt = max(1, (n_sv + 255) // 256)
+    out = {1}
+    for sp in range(1, nt + 1):
+        tps = (nt + sp - 1) // sp
+        if (nt + tps - 1) // tps != sp:
+            continue
+        ctas = mt * sp
+        if ctas <= 2 * sms:
+            out.add(sp)
+    return sorted(out)[-6:] if len(out) > 6 else sorted(out)
+
+
+def _load_cache():
+    try:
+        with open(CACHE_PATH) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store_cache(cache):
+    try:
+        os.makedirs(os.path.dirname(CACHE_PATH), exist_ok=True)
+        tmp = CACHE_PATH + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE_PATH)
+    except OSError:
+        pass
+
+
+def tune(ctx, key, stage1, stage2, n_rows, n_sv, stream, use_cache=True, tensor_core=True):
+    """Pick the fastest Tuning for the workload `key` (stage1 / stage2 enqueue the two stages
+    on `stream`).  Returns (tuning, report)."""
+    dev = torch.cuda.get_device_name()
+    full_key = f"{dev}|{key}"
+    cache = _load_cache() if use_cache else {}
+    if full_key in cache:
+        t = Tuning(**cache[full_key]["tuning"])
+        t.apply(ctx)
+        return t, dict(cache[full_key], cached=True)
+    report = {"k1": {}, "k2": {}}
+    best = Tuning()
+    # K1: CTAs per SM
+    best_ms = None
+    for c in (2, 1):
+        ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, c)
+        ms = _time(stage1, stream)
+        report["k1"][c] = ms
+        if best_ms is None or ms < best_ms:
+            best_ms, best.lbp_ctas_per_sm = ms, c
+    ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, best.lbp_ctas_per_sm)
+    # K2: splits x multicast
+    if tensor_core:
+        best_ms = None
+        for sp in split_candidates(n_rows, n_sv, torch.cuda.get_device_properties(0).multi_processor_count):
+            for mc in (1, 2):
+                ctx.set_tuning(B.TUNE_TC_SPLITS, sp)
+                ctx.set_tuning(B.TUNE_TC_MULTICAST, mc)
+                ms = _time(stage2, stream)
+                report["k2"][f"{sp}/{'mc' if mc == 1 else 'nomc'}"] = ms
+                if best_ms is None or ms < best_ms:
+                    best_ms, best.tc_splits, best.tc_multicast = ms, sp, mc
+    best.apply(ctx)
+    entry = {"tuning": asdict(best), "report": report}
+    cache[full_key] = entry
+    if use_cache:
+        _store_cache(cache)
+    return best, dict(entry, cached=False)

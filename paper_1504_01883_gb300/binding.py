@@ -22,7 +22,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "rgbd_lbp.h")
 RGBD_OK = 0
 DT_F32, DT_BF16, DT_FP8, DT_TF32 = 1, 2, 3, 4
 KERNEL_LINEAR, KERNEL_RBF = 0, 1
-LBP_GE, LBP_NBR_IGNORE_MASK = 1, 2
+LBP_GE, LBP_NBR_IGNORE_MASK, LBP_FACE_HIST256 = 1, 2, 4
+TUNE_LBP_CTAS_PER_SM, TUNE_TC_SPLITS, TUNE_TC_MULTICAST = 1, 2, 3
 STATUS_BAD_RECT, STATUS_WAIT_TIMEOUT = 1, 2
 NBINS, CELL = 59, 8
 
@@ -74,6 +75,8 @@ def lib():
             "rgbd_svm_get_info": [P, P],
             "rgbd_svm_packed_sv": [P, P, P],
             "svm_score": [P, P, P, P, I, F, P, P, P],
+            "rgbd_ctx_set_tuning": [P, I, I],
+            "rgbd_track_nearest": [P, P, I, P, I, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -149,6 +152,9 @@ class Context:
     def reserve(self, nbytes: int):
         _check(lib().rgbd_ctx_reserve(self.handle, ctypes.c_size_t(nbytes)))
 
+    def set_tuning(self, key: int, value: int):
+        _check(lib().rgbd_ctx_set_tuning(self.handle, int(key), int(value)))
+
     def status(self, clear: bool = True) -> int:
         v = ctypes.c_uint32(0)
         _check(lib().rgbd_ctx_status(self.handle, ctypes.byref(v), 1 if clear else 0))
@@ -184,7 +190,9 @@ def lbp_fused_features(ctx, grey, depth, rects=None, crop=128, cell=CELL, mask_m
     """Returns (feats uint16-as-int16 [n][dim] or None, x [n][k_pad] or None, xsq [n] or None)."""
     F, H, W = grey.shape
     n = F if rects is None else rects.shape[0]
-    dim = (crop // cell) ** 2 * NBINS
+    if flags & LBP_FACE_HIST256:
+        cell = crop  # one histogram over the whole face
+    dim = 256 if flags & LBP_FACE_HIST256 else (crop // cell) ** 2 * NBINS
     dt = _dt(x_dtype)
     k_pad = k_pad_for(dim) if k_pad is None else k_pad
     out = out or {}
@@ -201,6 +209,16 @@ def lbp_fused_features(ctx, grey, depth, rects=None, crop=128, cell=CELL, mask_m
                                     mask_mm, flags, _p(f) if feats else None, dt, _p(x) if dt else None, k_pad,
                                     float(x_scale), _p(q) if (dt and xsq) else None, _stream(stream)))
     return (f if feats else None), (x if dt else None), (q if (dt and xsq) else None)
+
+
+def rgbd_track_nearest(ctx, prev, cur, match=None, stream=None):
+    """prev, cur: int32 [n][5] rects (frame = stream id).  Returns int32 [n_prev] indices into cur."""
+    n_prev, n_cur = prev.shape[0], cur.shape[0]
+    if match is None:
+        match = torch.empty((n_prev,), dtype=torch.int32, device=prev.device)
+    _check(lib().rgbd_track_nearest(ctx.handle, _p(prev), n_prev, _p(cur) if n_cur else None, n_cur, _p(match),
+                                    _stream(stream)))
+    return match
 
 
 def lbp_normalize_features(ctx, feats, x_dtype, k_pad=None, x_scale=448.0, nbins=NBINS, stream=None):

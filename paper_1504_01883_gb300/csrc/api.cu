@@ -135,6 +135,26 @@ int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear) {
     return RGBD_OK;
 }
 
+int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value) {
+    CHECK_ARG(ctx != nullptr, "rgbd_ctx_set_tuning: ctx is NULL");
+    CHECK_ARG(value >= 0, "rgbd_ctx_set_tuning: value %d < 0", value);
+    switch (key) {
+        case RGBD_TUNE_LBP_CTAS_PER_SM:
+            CHECK_ARG(value <= 2, "rgbd_ctx_set_tuning: %d CTAs per SM (0, 1 or 2)", value);
+            ctx->tune_lbp_ctas_per_sm = value;
+            return RGBD_OK;
+        case RGBD_TUNE_TC_SPLITS:
+            ctx->tune_tc_splits = value;
+            return RGBD_OK;
+        case RGBD_TUNE_TC_MULTICAST:
+            CHECK_ARG(value <= 2, "rgbd_ctx_set_tuning: multicast %d (0, 1 or 2)", value);
+            ctx->tune_tc_multicast = value;
+            return RGBD_OK;
+        default:
+            return set_error(RGBD_ERR_ARG, "rgbd_ctx_set_tuning: unknown key %d", key);
+    }
+}
+
 int rgbd_crop_affine(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, int n_frames, int H,
                      int W, const rgbd_rect* rects, const int32_t* affine_q16, int n_rects,
                      int out_h, int out_w, uint8_t* out_grey, uint16_t* out_depth, void* stream) {
@@ -172,18 +192,26 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
                        void* x_out, int k_pad, float x_scale, float* xsq_out, void* stream) {
     CHECK_ARG(ctx != nullptr, "lbp_fused_features: ctx is NULL");
     CHECK_ARG(n >= 0, "lbp_fused_features: n %d < 0", n);
-    if (cell != kCell)
-        return set_error(RGBD_ERR_UNSUPPORTED, "lbp_fused_features: cell %d (only 8)", cell);
-    if (crop != 32 && crop != 64 && crop != 96 && crop != 128)
-        return set_error(RGBD_ERR_UNSUPPORTED,
-                         "lbp_fused_features: crop %d (32, 64, 96 or 128)", crop);
-    CHECK_ARG(mask_mm > 0, "lbp_fused_features: mask_mm %d", mask_mm);
-    CHECK_ARG((flags & ~(RGBD_LBP_GE | RGBD_LBP_NBR_IGNORE_MASK)) == 0,
+    CHECK_ARG((flags & ~(RGBD_LBP_GE | RGBD_LBP_NBR_IGNORE_MASK | RGBD_LBP_FACE_HIST256)) == 0,
               "lbp_fused_features: unknown flags 0x%x", flags);
+    const bool face256 = (flags & RGBD_LBP_FACE_HIST256) != 0;
+    if (face256) {
+        if (cell != crop)
+            return set_error(RGBD_ERR_UNSUPPORTED, "lbp_fused_features: the 0-255 face histogram needs cell == crop");
+        if (crop < 8 || crop > 255)
+            return set_error(RGBD_ERR_UNSUPPORTED, "lbp_fused_features: crop %d (8..255 for the face histogram)", crop);
+    } else {
+        if (cell != kCell)
+            return set_error(RGBD_ERR_UNSUPPORTED, "lbp_fused_features: cell %d (only 8)", cell);
+        if (crop != 32 && crop != 64 && crop != 96 && crop != 128)
+            return set_error(RGBD_ERR_UNSUPPORTED,
+                             "lbp_fused_features: crop %d (32, 64, 96 or 128)", crop);
+    }
+    CHECK_ARG(mask_mm > 0, "lbp_fused_features: mask_mm %d", mask_mm);
     if (n == 0) return RGBD_OK;
     CHECK_ARG(grey && depth, "lbp_fused_features: NULL frame pointer");
     CHECK_ARG(feats || x_out, "lbp_fused_features: neither feats nor x_out given");
-    const int dim = (crop / kCell) * (crop / kCell) * kBins;
+    const int dim = face256 ? 256 : (crop / kCell) * (crop / kCell) * kBins;
     int rc = check_x_out("lbp_fused_features", dim, x_dtype, x_out, k_pad, x_scale);
     if (rc) return rc;
     if (rects == nullptr) {

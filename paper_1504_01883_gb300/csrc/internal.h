@@ -28,6 +28,9 @@ struct DeviceProps {
 
 struct rgbd_ctx {
     rgbd::DeviceProps props;
+    int tune_lbp_ctas_per_sm = 0;  // 0 = occupancy limit
+    int tune_tc_splits = 0;        // 0 = cost model
+    int tune_tc_multicast = 0;     // 0 = auto, 1 = on, 2 = off
     uint32_t* d_status = nullptr;  // device status word
     void* workspace = nullptr;
     size_t workspace_bytes = 0;
@@ -48,7 +51,8 @@ struct rgbd_svm {
     uint16_t* coef_bf16 = nullptr;  // RBF tensor path: bf16 bits [C_pad][n_pad]
     float* asum = nullptr;    // [C] sum_i a_ci (accumulated in fp64)
     float* bias = nullptr;    // [C]
-    CUtensorMap tm_sv;        // tensor-core path: TMA descriptors
+    CUtensorMap tm_sv;        // tensor-core path: TMA descriptors (a whole SV tile, ...
+    CUtensorMap tm_sv_half;   // ... half of it, for the multicast of a CTA pair)
     CUtensorMap tm_coef;
     bool has_tmaps = false;
 };

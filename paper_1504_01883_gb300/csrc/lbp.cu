@@ -242,42 +242,36 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            // high-byte histogram of the non-zero depths, warp-aggregated when a warp's values
-            // fall in at most two neighbouring bins
+            // high-byte histogram of the non-zero depths.  The warp's two lowest bins (the face,
+            // which is nearer than the background) are counted with warp reductions and one
+            // atomic each; only the other values (background, spread over many bins) use
+            // per-value atomics, so no bin sees many same-address atomics in one instruction.
             const uint32_t d01 = dreg[2 * k], d23 = dreg[2 * k + 1];
             const uint32_t dv4[4] = {d01 & 0xFFFFu, d01 >> 16, d23 & 0xFFFFu, d23 >> 16};
-            int kmin = 256, kmax = -1;
+            int kmin = 256;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (dv4[e]) {
-                    const int key = (int)(dv4[e] >> 8);
-                    kmin = min(kmin, key);
-                    kmax = max(kmax, key);
-                }
-            }
+            for (int e = 0; e < 4; ++e)
+                if (dv4[e]) kmin = min(kmin, (int)(dv4[e] >> 8));
             const int wmin = __reduce_min_sync(FULL, kmin);
-            const int wmax = __reduce_max_sync(FULL, kmax);
-            if (wmax >= 0) {
-                if (wmax - wmin <= 1) {
-                    unsigned clo = 0, chi = 0;
+            if (wmin < 256) {
+                unsigned clo = 0, chi = 0;
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (dv4[e]) {
-                            const int key = (int)(dv4[e] >> 8);
-                            clo += key == wmin;
-                            chi += (key == wmax) && (wmax != wmin);
-                        }
+                for (int e = 0; e < 4; ++e) {
+                    if (dv4[e]) {
+                        const int key = (int)(dv4[e] >> 8);
+                        if (key == wmin)
+                            ++clo;
+                        else if (key == wmin + 1)
+                            ++chi;
+                        else
+                            atomicAdd(&sm.h1[key], 1u);
                     }
-                    const unsigned tlo = __reduce_add_sync(FULL, clo);
-                    const unsigned thi = __reduce_add_sync(FULL, chi);
-                    if (lane == 0) {
-                        atomicAdd(&sm.h1[wmin], tlo);
-                        if (thi) atomicAdd(&sm.h1[wmax], thi);
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (dv4[e]) atomicAdd(&sm.h1[dv4[e] >> 8], 1u);
+                }
+                const unsigned tlo = __reduce_add_sync(FULL, clo);
+                const unsigned thi = __reduce_add_sync(FULL, chi);
+                if (lane == 0) {
+                    atomicAdd(&sm.h1[wmin], tlo);
+                    if (thi) atomicAdd(&sm.h1[wmin + 1], thi);
                 }
             }
         }
@@ -545,6 +539,237 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
 }
 
 // ---------------------------------------------------------------------------------------
+// Section 3's own descriptor: one 0-255 histogram of the raw LBP codes per face (crop up to
+// 255 x 255; the paper uses 200 x 200).  Same resample, median mask and codes as the fused
+// kernel, written plainly (one pixel per thread step): this is the paper-literal variant, not
+// the throughput path.  One CTA of 1024 threads per face, persistent over faces.
+// ---------------------------------------------------------------------------------------
+constexpr int F256_THREADS = 1024;
+constexpr int F256_COPIES = 8;  // histogram copies (warp % 8) to spread same-code atomics
+
+__global__ void __launch_bounds__(F256_THREADS, 1) lbp_face256_kernel(LbpArgs a) {
+    const int S = a.crop, SS = S * S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t* depth = reinterpret_cast<uint16_t*>(smem_raw);           // [SS], later the mask bytes
+    uint8_t* grey = smem_raw + 2 * ((SS + 7) & ~7);                     // [SS]
+    uint32_t* hist = reinterpret_cast<uint32_t*>(grey + ((SS + 15) & ~15));  // [COPIES][256]
+    uint2* colmap = reinterpret_cast<uint2*>(hist + F256_COPIES * 256);     // [S]
+    uint2* rowmap = colmap + S;                                             // [S]
+    uint32_t* h1 = reinterpret_cast<uint32_t*>(rowmap + S);                 // [256]
+    uint32_t* h2 = h1 + 256;                                                // [256]
+    int* info = reinterpret_cast<int*>(h2 + 256);                           // [4]
+    float* red = reinterpret_cast<float*>(info + 4);                        // [32]
+    uint8_t* mask = reinterpret_cast<uint8_t*>(depth);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool strict = !(a.flags & RGBD_LBP_GE);
+    const bool nbr_ignore = (a.flags & RGBD_LBP_NBR_IGNORE_MASK) != 0;
+    const int x_dtype = a.x_out ? a.x_dtype : 0;
+    const int iters = (SS + F256_THREADS - 1) / F256_THREADS;
+
+    for (int face = blockIdx.x; face < a.n; face += gridDim.x) {
+        __syncthreads();
+        bool ok = true;
+        rgbd_rect r = {0, 0, 0, S, S};
+        const uint8_t* gsrc = a.grey;
+        const uint16_t* dsrc = a.depth;
+        int64_t aff[6] = {0, 0, 0, 0, 0, 0};
+        if (a.rects) {
+            r = a.rects[face];
+            ok = r.frame >= 0 && r.frame < a.n_frames && r.w > 0 && r.h > 0;
+            if (!ok && tid == 0) atomicOr(a.status, RGBD_STATUS_BAD_RECT);
+            if (ok) {
+                gsrc += (size_t)r.frame * a.H * a.W;
+                dsrc += (size_t)r.frame * a.H * a.W;
+                if (a.affine) {
+                    for (int i = 0; i < 6; ++i) aff[i] = a.affine[6 * (size_t)face + i];
+                } else {
+                    for (int i = tid; i < 2 * S; i += F256_THREADS) {
+                        if (i < S)
+                            colmap[i] = make_tap(rect_coord_q16(r.x, r.w, S, i), a.W);
+                        else
+                            rowmap[i - S] = make_tap(rect_coord_q16(r.y, r.h, S, i - S), a.H);
+                    }
+                }
+            }
+        } else {
+            gsrc += (size_t)face * SS;
+            dsrc += (size_t)face * SS;
+        }
+        for (int i = tid; i < F256_COPIES * 256; i += F256_THREADS) hist[i] = 0;
+        for (int i = tid; i < 256; i += F256_THREADS) {
+            h1[i] = 0;
+            h2[i] = 0;
+        }
+        __syncthreads();
+        // resample and the depth high-byte histogram
+        for (int it = 0; it < iters; ++it) {
+            const int pidx = tid + it * F256_THREADS;
+            uint32_t d = 0;
+            if (pidx < SS && ok) {
+                const int v = pidx / S, u = pidx - v * S;
+                uint32_t g;
+                if (!a.rects) {
+                    g = gsrc[pidx];
+                    d = dsrc[pidx];
+                } else if (!a.affine) {
+                    const uint2 tx = colmap[u], ty = rowmap[v];
+                    g = bilerp(gsrc, a.W, tx.x, ty.x);
+                    d = __ldg(dsrc + (size_t)ty.y * a.W + tx.y);
+                } else {
+                    const int64_t xq = aff[0] * u + aff[1] * v + aff[2];
+                    const int64_t yq = aff[3] * u + aff[4] * v + aff[5];
+                    const uint2 tx = make_tap(xq, a.W), ty = make_tap(yq, a.H);
+                    g = bilerp(gsrc, a.W, tx.x, ty.x);
+                    d = __ldg(dsrc + (size_t)ty.y * a.W + tx.y);
+                }
+                grey[pidx] = (uint8_t)g;
+            }
+            if (pidx < SS) depth[pidx] = (uint16_t)d;
+            if (d) atomicAdd(&h1[d >> 8], 1u);
+        }
+        __syncthreads();
+        // lower median of the non-zero depths (radix select over the high, then low byte)
+        if (warp == 0) {
+            uint32_t c = 0;
+            for (int i = lane; i < 256; i += 32) c += h1[i];
+            for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(FULL, c, off);
+            if (lane == 0) {
+                int b1 = -1, k1 = 0;
+                if (c > 0) {
+                    const uint32_t k = (c - 1) / 2;
+                    uint32_t acc = 0;
+                    for (int b = 0; b < 256; ++b) {
+                        if (k < acc + h1[b]) {
+                            b1 = b;
+                            k1 = (int)(k - acc);
+                            break;
+                        }
+                        acc += h1[b];
+                    }
+                }
+                info[0] = b1;
+                info[1] = k1;
+            }
+        }
+        __syncthreads();
+        const int b1 = info[0];
+        int med = -1;
+        if (b1 >= 0) {
+            for (int pidx = tid; pidx < SS; pidx += F256_THREADS) {
+                const uint32_t d = depth[pidx];
+                if (d && (int)(d >> 8) == b1) atomicAdd(&h2[d & 255u], 1u);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const uint32_t k1 = (uint32_t)info[1];
+                uint32_t acc = 0;
+                int b2 = 0;
+                for (int b = 0; b < 256; ++b) {
+                    if (k1 < acc + h2[b]) {
+                        b2 = b;
+                        break;
+                    }
+                    acc += h2[b];
+                }
+                info[2] = b1 * 256 + b2;
+            }
+            __syncthreads();
+            med = info[2];
+        }
+        // mask: valid bits to registers first, then bytes over the depth buffer
+        uint32_t vbits[4] = {0, 0, 0, 0};  // up to 128 pixels per thread (255^2 / 1024 < 64)
+        for (int it = 0; it < iters; ++it) {
+            const int pidx = tid + it * F256_THREADS;
+            if (pidx < SS) {
+                const int d = depth[pidx];
+                const int diff = d - med;
+                if (med >= 0 && d != 0 && diff < a.mask_mm && -diff < a.mask_mm) vbits[it >> 5] |= 1u << (it & 31);
+            }
+        }
+        __syncthreads();
+        for (int it = 0; it < iters; ++it) {
+            const int pidx = tid + it * F256_THREADS;
+            if (pidx < SS) mask[pidx] = (uint8_t)((vbits[it >> 5] >> (it & 31)) & 1u);
+        }
+        __syncthreads();
+        // codes and the 0-255 histogram
+        uint32_t* myh = hist + (warp % F256_COPIES) * 256;
+        for (int pidx = tid; pidx < SS; pidx += F256_THREADS) {
+            if (!mask[pidx]) continue;
+            const int i = pidx / S, j = pidx - i * S;
+            const int gc = grey[pidx];
+            int code = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                // ring p0..p7 clockwise from the top-left neighbour, y down
+                const int dx = (q == 0 || q == 6 || q == 7) ? -1 : ((q == 1 || q == 5) ? 0 : 1);
+                const int dy = (q <= 2) ? -1 : ((q == 3 || q == 7) ? 0 : 1);
+                const int rr = min(max(i + dy, 0), S - 1), cc = min(max(j + dx, 0), S - 1);
+                const int gp = grey[rr * S + cc];
+                const bool nb = nbr_ignore || mask[rr * S + cc];
+                if (nb && (strict ? gp > gc : gp >= gc)) code |= 1 << q;
+            }
+            atomicAdd(&myh[code], 1u);
+        }
+        __syncthreads();
+        // merge the copies, write counts, the normalised row and its squared norm
+        uint32_t cnt = 0;
+        if (tid < 256) {
+            for (int k = 0; k < F256_COPIES; ++k) cnt += hist[k * 256 + tid];
+            hist[tid] = cnt;  // copy 0 now holds the totals (each thread owns its bin)
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t t = 0;
+            for (int i = lane; i < 256; i += 32) t += hist[i];
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(FULL, t, off);
+            if (lane == 0) info[3] = (int)t;
+        }
+        __syncthreads();
+        const uint32_t nvalid = (uint32_t)info[3];
+        float sq = 0.f;
+        const int len = x_dtype ? a.k_pad : 256;
+        for (int j = tid; j < len; j += F256_THREADS) {
+            const uint32_t h = j < 256 ? hist[j] : 0u;
+            if (j < 256 && a.feats) a.feats[(size_t)face * 256 + j] = (uint16_t)h;
+            if (x_dtype) {
+                const float x = (j < 256 && nvalid) ? (float)h / (float)nvalid : 0.f;
+                const size_t idx = (size_t)face * a.k_pad + j;
+                float qv = x;
+                if (x_dtype == RGBD_DT_BF16) {
+                    const __nv_bfloat16 b = __float2bfloat16_rn(x);
+                    reinterpret_cast<uint16_t*>(a.x_out)[idx] = __bfloat16_as_ushort(b);
+                    qv = __bfloat162float(b);
+                } else if (x_dtype == RGBD_DT_FP8) {
+                    const __nv_fp8_e4m3 b(x * a.x_scale);
+                    reinterpret_cast<uint8_t*>(a.x_out)[idx] = b.__x;
+                    qv = static_cast<float>(b) * (1.0f / a.x_scale);
+                } else {
+                    reinterpret_cast<float*>(a.x_out)[idx] = x;
+                }
+                sq = fmaf(qv, qv, sq);
+            }
+        }
+        if (a.xsq) {
+            for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(FULL, sq, off);
+            if (lane == 0) red[warp] = sq;
+            __syncthreads();
+            if (tid == 0) {
+                float t = 0.f;
+                for (int w = 0; w < F256_THREADS / 32; ++w) t += red[w];
+                a.xsq[face] = t;
+            }
+        }
+    }
+}
+
+size_t face256_smem(int S) {
+    const size_t SS = (size_t)S * S;
+    return 2 * ((SS + 7) & ~size_t(7)) + ((SS + 15) & ~size_t(15)) + 4 * F256_COPIES * 256 + 2 * 8 * (size_t)S +
+           4 * 512 + 16 + 4 * 32;
+}
+
+// ---------------------------------------------------------------------------------------
 // Plain crop (rgbd_crop_affine): one thread per crop pixel.
 // ---------------------------------------------------------------------------------------
 __global__ void crop_affine_kernel(const uint8_t* __restrict__ grey, const uint16_t* __restrict__ depth,
@@ -680,7 +905,8 @@ int launch_fused_t(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: occupancy");
         blocks_per_sm = b > 0 ? b : 1;
     }
-    const int grid = (int)std::min<long long>((long long)a.n, (long long)blocks_per_sm * ctx->props.sm_count);
+    const int per_sm = ctx->tune_lbp_ctas_per_sm > 0 ? std::min(ctx->tune_lbp_ctas_per_sm, blocks_per_sm) : blocks_per_sm;
+    const int grid = (int)std::min<long long>((long long)a.n, (long long)per_sm * ctx->props.sm_count);
     lbp_fused_kernel<S><<<grid, Cfg<S>::NT, smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: launch");
@@ -690,6 +916,17 @@ int launch_fused_t(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
 }  // namespace
 
 int launch_lbp_fused(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
+    if (a.flags & RGBD_LBP_FACE_HIST256) {
+        const size_t smem = face256_smem(a.crop);
+        cudaError_t e = cudaFuncSetAttribute(lbp_face256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: 0-255 histogram smem attribute");
+        const int grid = std::min(a.n, ctx->props.sm_count);
+        lbp_face256_kernel<<<grid, F256_THREADS, smem, s>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: 0-255 histogram launch");
+        return RGBD_OK;
+    }
     switch (a.crop) {
         case 32: return launch_fused_t<32>(ctx, a, s);
         case 64: return launch_fused_t<64>(ctx, a, s);

@@ -136,6 +136,30 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
+// TMA load multicast to the CTAs of `mask` in the cluster: same CTA-relative destination offset
+// and mbarrier in each of them.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -193,6 +217,10 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 // ---------------------------------------------------------------------------------------
 // The kernel
 // ---------------------------------------------------------------------------------------
+// MC: the CTA runs in a cluster of two along the rows.  Both CTAs use the same SV tiles, so each
+// loads half of every SV k-block and multicasts it into both CTAs' stage, and each CTA's MMA
+// releases the stage in both CTAs: the pair reads each SV k-block from L2 once.
+template <bool MC>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     rbf_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_sv,
                   const __grid_constant__ CUtensorMap tm_coef, const TcParams p) {
@@ -216,7 +244,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             bar_init(bar(B_FULL + s), 1);
-            bar_init(bar(B_EMPTY + s), 1);
+            bar_init(bar(B_EMPTY + s), MC ? 2 : 1);  // both CTAs' MMAs read a multicast stage
         }
         bar_init(bar(B_GFULL), 1);
         bar_init(bar(B_GEMPTY), 8);
@@ -237,9 +265,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    __syncwarp();
+    if (MC)
+        cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
+    else
+        __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const uint32_t crank = MC ? cluster_rank() : 0u;
     const uint32_t coef_chunk_bytes = (uint32_t)p.C_pad * 128u;
 
     if (warp == 0) {
@@ -260,7 +293,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const uint32_t sa = base + (uint32_t)stage * STAGE_BYTES;
                     bar_arrive_tx(bar(B_FULL + stage), STAGE_BYTES);
                     tma_load_2d(sa, &tm_x, kb * p.k_elems, m0, bar(B_FULL + stage));
-                    tma_load_2d(sa + X_TILE, &tm_sv, kb * p.k_elems, n0, bar(B_FULL + stage));
+                    if (MC)
+                        tma_load_2d_mc(sa + X_TILE + crank * (SV_TILE / 2), &tm_sv, kb * p.k_elems,
+                                       n0 + (int)crank * (BN / 2), bar(B_FULL + stage), (uint16_t)0x3);
+                    else
+                        tma_load_2d(sa + X_TILE, &tm_sv, kb * p.k_elems, n0, bar(B_FULL + stage));
                     armed |= 1u << stage;
                     armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
                     if (++stage == STAGES) {
@@ -363,7 +400,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         const uint64_t bd = sdesc(sa + X_TILE + ks * 32);
                         mma_issue(p.kind, tmem, a, bd, p.idesc_main, (kb > 0 || ks > 0) ? 1u : 0u);
                     }
-                    tc_commit(bar(B_EMPTY + stage));
+                    if (MC)
+                        tc_commit_mc(bar(B_EMPTY + stage), (uint16_t)0x3);
+                    else
+                        tc_commit(bar(B_EMPTY + stage));
                     if (++stage == STAGES) {
                         stage = 0;
                         phase ^= 1u;
@@ -503,7 +543,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
 
     tc_fence_before();
-    __syncthreads();
+    __syncwarp();
+    if (MC)
+        cluster_sync();  // no CTA leaves while its peer may still multicast into it or arrive on it
+    else
+        __syncthreads();
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
@@ -573,6 +617,9 @@ int pack_model_tensor_maps(rgbd_svm* m) {
     int rc = encode_tmap_2d(&m->tm_sv, dt, m->sv, (uint64_t)m->k_pad, (uint64_t)m->n_pad,
                             (uint64_t)m->k_pad * esz, 128u / esz, BN, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
+    rc = encode_tmap_2d(&m->tm_sv_half, dt, m->sv, (uint64_t)m->k_pad, (uint64_t)m->n_pad,
+                        (uint64_t)m->k_pad * esz, 128u / esz, BN / 2, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
     rc = encode_tmap_2d(&m->tm_coef, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m->coef_bf16, (uint64_t)m->n_pad,
                         (uint64_t)m->C_pad, (uint64_t)m->n_pad * 2, 64u, (uint32_t)m->C_pad,
                         CU_TENSOR_MAP_SWIZZLE_128B);
@@ -612,8 +659,10 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
     }
     pl->mt = (n + BM - 1) / BM;
     pl->nt = m->n_pad / BN;
-    pl->splits = choose_splits(pl->mt, pl->nt, ctx->props.sm_count);
+    pl->splits = ctx->tune_tc_splits > 0 ? std::min(ctx->tune_tc_splits, pl->nt)
+                                         : choose_splits(pl->mt, pl->nt, ctx->props.sm_count);
     pl->tps = (pl->nt + pl->splits - 1) / pl->splits;
+    pl->splits = (pl->nt + pl->tps - 1) / pl->tps;  // every split non-empty
     const size_t part_bytes = sizeof(float) * (size_t)pl->splits * n * m->C_pad;
     const size_t ref_bytes = sizeof(float) * (size_t)pl->splits * n;
     const size_t as_bytes = sizeof(float) * (size_t)pl->splits * m->C_pad;
@@ -632,7 +681,12 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     int rc = encode_tmap_2d(&tm_x, pl.dt, x, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * pl.esz,
                             128u / pl.esz, BM, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
-    cudaError_t e = cudaFuncSetAttribute(rbf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    // pairs of 128-row blocks share their SV tiles, unless tuned off
+    const bool mc = pl.mt >= 2 && ctx->tune_tc_multicast != 2;
+    cudaError_t e = mc ? cudaFuncSetAttribute(rbf_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              SMEM_BYTES)
+                       : cudaFuncSetAttribute(rbf_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              SMEM_BYTES);
     if (e != cudaSuccess) return cuda_error(e, "svm_score: tc smem attribute");
     TcParams p;
     p.n = n;
@@ -656,9 +710,25 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     asum_split_kernel<<<pl.splits, 128, 0, s>>>(m->coef, m->C, m->C_pad, m->n_pad, m->n_sv, pl.tps * BN, asplit);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "svm_score: asum split launch");
-    dim3 grid(pl.mt, pl.splits);
-    rbf_tc_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm_x, m->tm_sv, m->tm_coef, p);
-    e = cudaGetLastError();
+    if (mc) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)((pl.mt + 1) / 2 * 2), (unsigned)pl.splits, 1);
+        cfg.blockDim = dim3(NUM_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, rbf_tc_kernel<true>, tm_x, m->tm_sv_half, m->tm_coef, p);
+    } else {
+        dim3 grid(pl.mt, pl.splits);
+        rbf_tc_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm_x, m->tm_sv, m->tm_coef, p);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return cuda_error(e, "svm_score: tc launch");
     return launch_reduce_scores(part, ref, pl.splits, n, m->C, m->C_pad, m->asum, asplit, m->bias, m->gamma, scores,
                                 labels, s);

@@ -211,6 +211,18 @@ class BatchServer:
             self.admission.release(req.slot)
         report.batches += 1
 
+    def serve_one(self, stream, index):
+        """Serves frame `index` of `stream` alone (a batch of one frame); returns the request."""
+        req = FrameRequest(0.0, int(stream), int(index))
+        req.slot = self.admission.try_admit()
+        if req.slot < 0:
+            raise RuntimeError("no free frame slot")
+        self._upload(req)
+        b = self._launch([req], 0)
+        b.done.synchronize()
+        self._complete(b, time.perf_counter(), ServeReport(), keep_results=True)
+        return req
+
     def run(self, events, keep_results=False, realtime=True):
         """events: list of (t_arrival_s, stream, n_faces) sorted by time.  Returns (report, requests)."""
         counters = collections.Counter()

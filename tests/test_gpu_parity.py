@@ -216,3 +216,56 @@ def test_rbf_tensor_core_paths(B, ctx, orc, dt, n, n_sv, C):
     bound = {"tf32": 2e-5, "bf16": 5e-5, "fp8": 1e-3}[dt]
     print(f"{dt} n={n} n_sv={n_sv} C={C}: rel err {err:.3e}")
     assert err <= bound, err
+
+
+@pytest.mark.parametrize("splits,mc", [(1, 2), (3, 1), (8, 2)])
+def test_tuning_changes_layout_not_results(B, ctx, orc, splits, mc):
+    """Forced SV splits / multicast (the autotuner's knobs) keep the scores within tolerance."""
+    X, SV, a, b, gamma = _scoring_problem(5, 300, 2000, 16)
+    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype="bf16")
+    x, q = B.lbp_normalize_features(ctx, dev_u16(X), "bf16")
+    s0, _ = B.svm_score(ctx, model, x, q)
+    ctx.set_tuning(B.TUNE_TC_SPLITS, splits)
+    ctx.set_tuning(B.TUNE_TC_MULTICAST, mc)
+    try:
+        s1, _ = B.svm_score(ctx, model, x, q)
+    finally:
+        ctx.set_tuning(B.TUNE_TC_SPLITS, 0)
+        ctx.set_tuning(B.TUNE_TC_MULTICAST, 0)
+    scale = rbf_error_scale(orc.normalize_f64(X), orc.normalize_f64(SV), a, b, gamma)
+    assert rel_score_error(s1.cpu().numpy(), s0.cpu().numpy().astype(np.float64), scale) <= 1e-5
+
+
+# ---------------------------------------------------------------------------------------------
+# Section 3's 0-255 face histogram and Section 2.3's nearest-centre tracking
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("crop", [200, 57, 255])
+def test_face_histogram_256(B, ctx, orc, crop):
+    g, d, r = synth.frames_with_rects(17, 2, 3, 40, 260, H=240, W=320)
+    want = orc.features_batch(g, d, r, crop, cell=crop, nbins=256)
+    f, x, q = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=crop,
+                                   flags=B.LBP_FACE_HIST256, x_dtype="f32")
+    assert (host_u16(f) == want).all()
+    x32 = orc.normalize_f32(want, nbins=256)
+    assert (x.cpu().numpy()[:, :256].view(np.uint32) == x32.view(np.uint32)).all()
+    # pre-cut 200x200 crops, the paper's face size
+    gc, dc = synth.crops(4, 2, 200)
+    want2 = orc.features_batch(gc, dc, None, 200, cell=200, nbins=256)
+    f2, _, _ = B.lbp_fused_features(ctx, dev_u8(gc), dev_u16(dc), None, crop=200, flags=B.LBP_FACE_HIST256)
+    assert (host_u16(f2) == want2).all()
+
+
+def test_track_nearest(B, ctx, orc):
+    rng = np.random.default_rng(5)
+    R = synth.RECT_DTYPE
+    prev = np.zeros(300, R)
+    cur = np.zeros(280, R)
+    for arr in (prev, cur):
+        arr["frame"] = rng.integers(0, 32, len(arr))
+        arr["x"] = rng.integers(-50, 600, len(arr))
+        arr["y"] = rng.integers(-50, 450, len(arr))
+        arr["w"] = rng.integers(48, 257, len(arr))
+        arr["h"] = arr["w"]
+    m = B.rgbd_track_nearest(ctx, B.rects_tensor(prev), B.rects_tensor(cur))
+    assert (m.cpu().numpy() == orc.track_nearest(prev, cur)).all()

@@ -336,3 +336,41 @@ def test_features_batch_composes_steps(orc):
     bad[1]["frame"] = 5
     f2 = orc.features_batch(g, d, bad, out_h=64)
     assert not f2[1].any() and (f2[0] == feats[0]).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# Section 2.3: nearest-centre tracking
+# ---------------------------------------------------------------------------------------------
+
+def test_track_nearest_hand_cases(orc):
+    R = orc.RECT_DTYPE
+    # stream 0: A at centre (50, 50); the next frame has faces at centres (60, 50), (45, 58), (200, 10)
+    prev = np.array([(0, 40, 40, 20, 20), (1, 0, 0, 10, 10), (0, 190, 0, 20, 20)], R)
+    cur = np.array([(0, 50, 40, 20, 20), (0, 35, 48, 20, 20), (0, 190, 0, 20, 20), (2, 0, 0, 4, 4)], R)
+    m = orc.track_nearest(prev, cur)
+    # A: distances 10 and sqrt(25 + 64) = 9.43 -> index 1; stream 1 has no current face -> -1;
+    # the third face sits exactly on cur[2] -> 2
+    assert list(m) == [1, -1, 2]
+    # a tie (both at distance 5) keeps the lower index
+    cur2 = np.array([(0, 45, 40, 20, 20), (0, 35, 40, 20, 20)], R)
+    assert list(orc.track_nearest(prev[:1], cur2)) == [0]
+    # brute force with numpy on random layouts
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        p = np.zeros(7, R)
+        c = np.zeros(9, R)
+        for arr in (p, c):
+            arr["frame"] = rng.integers(0, 3, len(arr))
+            arr["x"] = rng.integers(-50, 600, len(arr))
+            arr["y"] = rng.integers(-50, 450, len(arr))
+            arr["w"] = rng.integers(10, 200, len(arr))
+            arr["h"] = arr["w"]
+        got = orc.track_nearest(p, c)
+        for i in range(len(p)):
+            same = np.nonzero(c["frame"] == p[i]["frame"])[0]
+            if same.size == 0:
+                assert got[i] == -1
+                continue
+            d = np.hypot((c["x"][same] + c["w"][same] / 2) - (p["x"][i] + p["w"][i] / 2),
+                         (c["y"][same] + c["h"][same] / 2) - (p["y"][i] + p["h"][i] / 2))
+            assert got[i] == same[np.argmin(d)]

@@ -1,0 +1,62 @@
+"""The continuous-batching request loop: admission by memory (host logic, CPU) and, on the GPU,
+every frame's scores are the same when served alone as in the mix of a busy run."""
+import numpy as np
+import pytest
+
+from paper_1504_01883_gb300 import synth
+
+
+def test_admission_waits_for_memory_and_slots():
+    torch = pytest.importorskip("torch")  # noqa: F841 (serve imports torch)
+    from paper_1504_01883_gb300.serve import MemoryAdmission
+    free = {"bytes": 1 << 30}
+    adm = MemoryAdmission(2, reserve_bytes=512 << 20, mem_get_info=lambda: (free["bytes"], 1 << 34))
+    a, b = adm.try_admit(), adm.try_admit()
+    assert {a, b} == {0, 1}
+    assert adm.try_admit() == -1           # no slot
+    adm.release(a)
+    free["bytes"] = 100 << 20              # the device is short of memory (a fake mem_get_info)
+    assert adm.try_admit() == -1 and adm.rejections == 1
+    free["bytes"] = 1 << 30
+    assert adm.try_admit() == a
+
+
+def test_arrivals_are_seeded_and_ordered():
+    ev = synth.serving_arrivals(seed=3, n_streams=4, seconds=1.0)
+    assert ev == sorted(ev)
+    assert ev == synth.serving_arrivals(seed=3, n_streams=4, seconds=1.0)
+    assert all(1 <= k <= 12 for _, _, k in ev)
+    assert 60 < len(ev) < 200  # about 4 x 30 per second
+
+
+@pytest.mark.gpu
+def test_each_frame_is_the_same_alone_and_in_the_mix():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1504_01883_gb300 import _build, serve
+    from paper_1504_01883_gb300 import binding as B
+    _build.build()
+    ctx = B.Context(0)
+    dim = 16 * 16 * 59
+    rng = synth.rng_for(99)
+    sv = synth.poisson_counts(rng, 1024, dim)
+    a, b = synth.rbf_coefficients(rng, 16, 1024)
+    model = B.svm_train_data_pack(ctx, torch.from_numpy(sv.view(np.int16)).cuda(), torch.from_numpy(a).cuda(),
+                                  torch.from_numpy(b).cuda(), gamma=1.0 / dim, dtype="bf16")
+    streams = serve.make_streams(seed=7, n_streams=6, frames_per_stream=2)
+    events = synth.serving_arrivals(seed=7, n_streams=6, seconds=0.3)
+    srv = serve.BatchServer(ctx, model, streams, n_slots=24, max_faces=512)
+    rep, reqs = srv.run(events, keep_results=True, realtime=False)  # everything at once: big mixed batches
+    assert rep.frames == len(events) and rep.batches < len(events)
+    alone = serve.BatchServer(ctx, model, streams, n_slots=2, max_faces=16)
+    scale = np.abs(a).sum(1)[None, :] + np.abs(b)[None, :]
+    for req in reqs[:: max(1, len(reqs) // 12)]:
+        one = alone.serve_one(req.stream, req.index)
+        assert one.n_faces == req.n_faces
+        assert np.max(np.abs(one.scores - req.scores) / scale) <= 5e-5
+        # labels are unique where the top two classes are further apart than the tolerance
+        srt = np.sort(req.scores, axis=1)
+        clear = (srt[:, -1] - srt[:, -2]) > 5e-5 * scale.max()
+        assert (one.labels[clear] == req.labels[clear]).all()
+    assert ctx.status() == 0
