@@ -185,7 +185,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--score-dtype", default="tf32", choices=["tf32", "bf16", "fp8", "f32"])
+    ap.add_argument("--score-dtype", default="bf16", choices=["bf16", "tf32", "fp8", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-crops-per-step", type=int, default=8)
     ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision"],

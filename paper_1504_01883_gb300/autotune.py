@@ -56,15 +56,14 @@ def split_candidates(n_rows, n_sv, sms=152):
     """Split counts worth timing: the cost model's neighbourhood of whole-wave layouts."""
     mt = (n_rows + 127) // 128
     nt = max(1, (n_sv + 255) // 256)
-    out = {1}
+    out = []
     for sp in range(1, nt + 1):
         tps = (nt + sp - 1) // sp
         if (nt + tps - 1) // tps != sp:
-            continue
-        ctas = mt * sp
-        if ctas <= 2 * sms:
-            out.add(sp)
-    return sorted(out)[-6:] if len(out) > 6 else sorted(out)
+            continue  # not an exact split count
+        if mt * sp <= 4 * sms:
+            out.append(sp)
+    return out[-8:] if len(out) > 8 else out
 
 
 def _load_cache():
