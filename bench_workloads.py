@@ -194,7 +194,7 @@ def run_precision(args):
     labels = {}
     sub_scores = {}
     x_scale = 448.0
-    for dt in ["f32", "bf16", "fp8", "tf32"]:
+    for dt in ["f32", "bf16", "fp8", "tf32", "bf16x3"]:
         model = B.svm_train_data_pack(ctx, SV, at, bt, gamma=gamma, dtype=dt)
         x, q = B.lbp_normalize_features(ctx, X, dt, x_scale=x_scale)
         s_out, l_out = B.svm_score(ctx, model, x, q, x_scale=x_scale)
@@ -210,7 +210,7 @@ def run_precision(args):
             ts.append(e0.elapsed_time(e1))
         ms = float(np.median(ts))
         flops = 2.0 * n_rows * n_sv * dim + 2.0 * n_rows * n_sv * C
-        ratio = {"bf16": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25}.get(dt)
+        ratio = {"bf16": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25, "bf16x3": 1.0 / 3.0}.get(dt)
         peak = pk["bf16_tflops"] * ratio if ratio else None
         res[dt] = {"ms": ms, "tflops": flops / ms / 1e9, "frac_of_peak": (flops / ms / 1e9) / peak if peak else None,
                    "peak_tflops": peak}

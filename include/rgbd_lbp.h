@@ -54,6 +54,10 @@ extern "C" {
 #define RGBD_DT_BF16 2 /* bfloat16 storage, scored on tcgen05 tensor cores, fp32 accumulate */
 #define RGBD_DT_FP8 3  /* FP8 E4M3 storage with a per-tensor scale, tcgen05, fp32 accumulate */
 #define RGBD_DT_TF32 4 /* fp32 storage, scored on tcgen05 tensor cores as TF32 */
+#define RGBD_DT_BF16X3 5 /* two bfloat16 planes, hi = bf16(x) and lo = bf16(x - hi), so x = hi + lo
+                            to 2^-18; scored with three BF16 MMAs (hi.hi + hi.lo + lo.hi), fp32
+                            accumulate.  A row buffer holds the hi plane [n][k_pad] followed by
+                            the lo plane [n][k_pad]. */
 
 /* ---- SVM kernels ------------------------------------------------------------------------- */
 #define RGBD_KERNEL_LINEAR 0 /* S_c = w_c . x + b_c */
@@ -121,7 +125,10 @@ int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear);
  * path; scores change within rounding (the split of the SV sum).
  *   RGBD_TUNE_LBP_CTAS_PER_SM   resident fused-kernel CTAs per SM (1 or 2)
  *   RGBD_TUNE_TC_SPLITS         SV-tile ranges per 128-row block in tensor-core scoring
- *   RGBD_TUNE_TC_MULTICAST      1 = CTA pairs share SV tiles by TMA multicast, 2 = off
+ *   RGBD_TUNE_TC_MULTICAST      CTA pairing of 128-row blocks in tensor-core scoring:
+ *                               0 = default (3), 1 = pairs share SV tiles by TMA multicast,
+ *                               2 = no pairing, 3 = each pair runs one 256-row MMA
+ *                               (tcgen05 cta_group::2, each CTA holding half of the SV tile)
  * Errors: RGBD_ERR_ARG for an unknown key or a negative value. */
 #define RGBD_TUNE_LBP_CTAS_PER_SM 1
 #define RGBD_TUNE_TC_SPLITS 2

@@ -40,6 +40,9 @@ class Tuning:
         ctx.set_tuning(B.TUNE_TC_MULTICAST, self.tc_multicast)
 
 
+PAIRING_NAMES = {1: "mc", 2: "single", 3: "pair"}
+
+
 def _time(fn, stream, reps=3):
     ts = []
     for _ in range(reps + 1):
@@ -106,15 +109,15 @@ def tune(ctx, key, stage1, stage2, n_rows, n_sv, stream, use_cache=True, tensor_
         if best_ms is None or ms < best_ms:
             best_ms, best.lbp_ctas_per_sm = ms, c
     ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, best.lbp_ctas_per_sm)
-    # K2: splits x multicast
+    # K2: splits x CTA pairing
     if tensor_core:
         best_ms = None
         for sp in split_candidates(n_rows, n_sv, torch.cuda.get_device_properties(0).multi_processor_count):
-            for mc in (1, 2):
+            for mc in (3, 1, 2):
                 ctx.set_tuning(B.TUNE_TC_SPLITS, sp)
                 ctx.set_tuning(B.TUNE_TC_MULTICAST, mc)
                 ms = _time(stage2, stream)
-                report["k2"][f"{sp}/{'mc' if mc == 1 else 'nomc'}"] = ms
+                report["k2"][f"{sp}/{PAIRING_NAMES[mc]}"] = ms
                 if best_ms is None or ms < best_ms:
                     best_ms, best.tc_splits, best.tc_multicast = ms, sp, mc
     best.apply(ctx)

@@ -20,14 +20,15 @@ LIB_PATH = os.path.join(HERE, "librgbdlbp.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "rgbd_lbp.h")
 
 RGBD_OK = 0
-DT_F32, DT_BF16, DT_FP8, DT_TF32 = 1, 2, 3, 4
+DT_F32, DT_BF16, DT_FP8, DT_TF32, DT_BF16X3 = 1, 2, 3, 4, 5
 KERNEL_LINEAR, KERNEL_RBF = 0, 1
 LBP_GE, LBP_NBR_IGNORE_MASK, LBP_FACE_HIST256 = 1, 2, 4
 TUNE_LBP_CTAS_PER_SM, TUNE_TC_SPLITS, TUNE_TC_MULTICAST = 1, 2, 3
 STATUS_BAD_RECT, STATUS_WAIT_TIMEOUT = 1, 2
 NBINS, CELL = 59, 8
 
-_DT_NAMES = {"f32": DT_F32, "fp32": DT_F32, "bf16": DT_BF16, "fp8": DT_FP8, "e4m3": DT_FP8, "tf32": DT_TF32}
+_DT_NAMES = {"f32": DT_F32, "fp32": DT_F32, "bf16": DT_BF16, "fp8": DT_FP8, "e4m3": DT_FP8, "tf32": DT_TF32,
+             "bf16x3": DT_BF16X3}
 _lib = None
 
 
@@ -122,7 +123,13 @@ def _dt(x):
 
 def x_torch_dtype(dt):
     dt = _dt(dt)
-    return {DT_F32: torch.float32, DT_TF32: torch.float32, DT_BF16: torch.bfloat16, DT_FP8: torch.uint8}[dt]
+    return {DT_F32: torch.float32, DT_TF32: torch.float32, DT_BF16: torch.bfloat16, DT_FP8: torch.uint8,
+            DT_BF16X3: torch.bfloat16}[dt]
+
+
+def x_shape(dt, n, k_pad):
+    """Shape of a normalised-row buffer: split bf16 rows are two planes (hi, then lo)."""
+    return (2, n, k_pad) if _dt(dt) == DT_BF16X3 else (n, k_pad)
 
 
 def k_pad_for(dim: int) -> int:
@@ -201,7 +208,7 @@ def lbp_fused_features(ctx, grey, depth, rects=None, crop=128, cell=CELL, mask_m
         f = torch.empty((n, dim), dtype=torch.int16, device=grey.device)
     x = out.get("x")
     if dt and x is None:
-        x = torch.empty((n, k_pad), dtype=x_torch_dtype(dt), device=grey.device)
+        x = torch.empty(x_shape(dt, n, k_pad), dtype=x_torch_dtype(dt), device=grey.device)
     q = out.get("xsq")
     if dt and xsq and q is None:
         q = torch.empty((n,), dtype=torch.float32, device=grey.device)
@@ -225,7 +232,7 @@ def lbp_normalize_features(ctx, feats, x_dtype, k_pad=None, x_scale=448.0, nbins
     n, dim = feats.shape
     dt = _dt(x_dtype)
     k_pad = k_pad_for(dim) if k_pad is None else k_pad
-    x = torch.empty((n, k_pad), dtype=x_torch_dtype(dt), device=feats.device)
+    x = torch.empty(x_shape(dt, n, k_pad), dtype=x_torch_dtype(dt), device=feats.device)
     q = torch.empty((n,), dtype=torch.float32, device=feats.device)
     _check(lib().lbp_normalize_features(ctx.handle, _p(feats), n, dim, nbins, dt, _p(x), k_pad, float(x_scale),
                                         _p(q), _stream(stream)))
@@ -279,7 +286,7 @@ def svm_train_data_pack(ctx, sv_feats, coef, bias=None, kernel=KERNEL_RBF, gamma
 
 
 def svm_score(ctx, model, x, xsq=None, x_scale=448.0, scores=None, labels=None, want_labels=True, stream=None):
-    n = x.shape[0]
+    n = x.shape[-2]  # rows (a split bf16 buffer is [2][n][k_pad])
     C = model.info.n_classes
     if scores is None:
         scores = torch.empty((n, C), dtype=torch.float32, device=x.device)
@@ -303,7 +310,7 @@ def svm_score_noalloc(ctx, model, x, xsq, x_scale=448.0, scores=None, labels=Non
     P = ctypes.c_void_p
     fn.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_float, P, P, P]
     fn.restype = ctypes.c_int
-    n = x.shape[0]
+    n = x.shape[-2]  # rows (a split bf16 buffer is [2][n][k_pad])
     C = model.info.n_classes
     if scores is None:
         scores = torch.empty((n, C), dtype=torch.float32, device=x.device)

@@ -147,7 +147,7 @@ int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value) {
             ctx->tune_tc_splits = value;
             return RGBD_OK;
         case RGBD_TUNE_TC_MULTICAST:
-            CHECK_ARG(value <= 2, "rgbd_ctx_set_tuning: multicast %d (0, 1 or 2)", value);
+            CHECK_ARG(value <= 3, "rgbd_ctx_set_tuning: CTA pairing %d (0, 1, 2 or 3)", value);
             ctx->tune_tc_multicast = value;
             return RGBD_OK;
         default:
@@ -176,7 +176,7 @@ static int check_x_out(const char* fn, int dim, int x_dtype, const void* x_out, 
                        float x_scale) {
     if (x_dtype == 0) return RGBD_OK;
     CHECK_ARG(x_dtype == RGBD_DT_F32 || x_dtype == RGBD_DT_BF16 || x_dtype == RGBD_DT_FP8 ||
-                  x_dtype == RGBD_DT_TF32,
+                  x_dtype == RGBD_DT_TF32 || x_dtype == RGBD_DT_BF16X3,
               "%s: unknown x_dtype %d", fn, x_dtype);
     CHECK_ARG(x_out != nullptr, "%s: x_out is NULL", fn);
     CHECK_ARG(k_pad >= dim && k_pad % kKAlign == 0, "%s: k_pad %d must be >= %d and a multiple of %d",
@@ -240,6 +240,7 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
     a.x_out = x_out;
     a.k_pad = k_pad;
     a.x_scale = x_scale;
+    a.x_plane = (size_t)n * k_pad;
     a.xsq = xsq_out;
     a.status = ctx->d_status;
     return launch_lbp_fused(ctx, a, (cudaStream_t)stream);

@@ -12,6 +12,7 @@ namespace rgbd {
 constexpr int kBins = 59;     // uniform-pattern bins per cell (58 uniform + 1)
 constexpr int kCell = 8;      // cell side in pixels
 constexpr int kKAlign = 128;  // k_pad granularity (elements)
+constexpr int kSvTile = 256;  // SVs per tensor-core tile; n_pad is a multiple of it
 
 // Sets the thread's last error message (printf-style) and returns `code`.
 int set_error(int code, const char* fmt, ...);
@@ -30,7 +31,7 @@ struct rgbd_ctx {
     rgbd::DeviceProps props;
     int tune_lbp_ctas_per_sm = 0;  // 0 = occupancy limit
     int tune_tc_splits = 0;        // 0 = cost model
-    int tune_tc_multicast = 0;     // 0 = auto, 1 = on, 2 = off
+    int tune_tc_multicast = 0;     // CTA pairing: 0 = auto, 1 = multicast, 2 = none, 3 = 2-CTA MMA
     uint32_t* d_status = nullptr;  // device status word
     void* workspace = nullptr;
     size_t workspace_bytes = 0;
@@ -50,10 +51,14 @@ struct rgbd_svm {
     float* coef = nullptr;    // RBF: float [C][n_pad]; linear: float [C][k_pad]
     uint16_t* coef_bf16 = nullptr;  // RBF tensor path: bf16 bits [C_pad][n_pad]
     float* asum = nullptr;    // [C] sum_i a_ci (accumulated in fp64)
+    float* asum_tile = nullptr;  // RBF: [n_pad / kSvTile][C_pad] sum of a_ci over each SV tile (fp64)
     float* bias = nullptr;    // [C]
     CUtensorMap tm_sv;        // tensor-core path: TMA descriptors (a whole SV tile, ...
     CUtensorMap tm_sv_half;   // ... half of it, for the multicast of a CTA pair)
+    CUtensorMap tm_sv_lo;     // RGBD_DT_BF16X3: the same two maps over the lo plane
+    CUtensorMap tm_sv_lo_half;
     CUtensorMap tm_coef;
+    CUtensorMap tm_coef_half; // half of the classes of a coefficient chunk (2-CTA MMA pairs)
     bool has_tmaps = false;
 };
 
@@ -96,13 +101,16 @@ struct LbpArgs {
     void* x_out;
     int k_pad;
     float x_scale;
+    size_t x_plane;  // RGBD_DT_BF16X3: elements from the hi plane to the lo plane
     float* xsq;
     uint32_t* status;
 };
 int launch_lbp_fused(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s);
 
+// plane: RGBD_DT_BF16X3 offset (elements) of the lo plane; 0 means n * k_pad.
 int launch_normalize(const uint16_t* feats, int n, int dim, int nbins, int x_dtype, void* x_out,
-                     int k_pad, float x_scale, float* xsq, float* row_max, cudaStream_t s);
+                     int k_pad, float x_scale, float* xsq, float* row_max, cudaStream_t s,
+                     size_t plane = 0);
 
 int launch_quantize_f32(const float* src, int n, int k_pad, int x_dtype, void* dst, float scale,
                         float* sq, cudaStream_t s);
@@ -128,10 +136,12 @@ int pack_model_tensor_maps(rgbd_svm* m);
 // Final reduction of per-split partial scores (svm_simt.cu), shared by both RBF paths.
 //   part  [splits][n][C_stride] partial sums D_s[k][c]
 //   ref   NULL, or [splits][n] per-split reference distances r_s (see svm_tc.cu)
+//   asum_tile  with ref: [n_tiles][C_stride] coefficient sums per SV tile; split s covers
+//              tiles [s * tiles_per_split, (s + 1) * tiles_per_split) clipped to n_tiles
 int launch_reduce_scores(const float* part, const float* ref, int splits, int n, int C,
-                         int C_stride, const float* asum, const float* asum_split,
-                         const float* bias, float gamma, float* scores, int32_t* labels,
-                         cudaStream_t s);
+                         int C_stride, const float* asum, const float* asum_tile,
+                         int tiles_per_split, int n_tiles, const float* bias, float gamma,
+                         float* scores, int32_t* labels, cudaStream_t s);
 
 // TMA descriptor encoding through the driver entry point (no libcuda link).
 int encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,

@@ -503,6 +503,24 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     }
                     *reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(a.x_out) +
                                               (size_t)face * a.k_pad + j) = make_uint2(pk[0], pk[1]);
+                } else if (x_dtype == RGBD_DT_BF16X3) {
+                    // hi = bf16(x) into the first plane, lo = bf16(x - hi) into the second
+                    uint32_t ph[2], pl[2];
+#pragma unroll
+                    for (int e = 0; e < 4; e += 2) {
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[e]), h1 = __float2bfloat16_rn(x[e + 1]);
+                        const float hf0 = __bfloat162float(h0), hf1 = __bfloat162float(h1);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[e] - hf0);
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[e + 1] - hf1);
+                        const float v0 = hf0 + __bfloat162float(l0), v1 = hf1 + __bfloat162float(l1);
+                        sq = fmaf(v0, v0, sq);
+                        sq = fmaf(v1, v1, sq);
+                        ph[e >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                        pl[e >> 1] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                    }
+                    uint16_t* xb = reinterpret_cast<uint16_t*>(a.x_out) + (size_t)face * a.k_pad + j;
+                    *reinterpret_cast<uint2*>(xb) = make_uint2(ph[0], ph[1]);
+                    *reinterpret_cast<uint2*>(xb + a.x_plane) = make_uint2(pl[0], pl[1]);
                 } else if (x_dtype == RGBD_DT_FP8) {
                     uint32_t pk = 0;
                     const float inv = 1.0f / a.x_scale;
@@ -740,6 +758,12 @@ __global__ void __launch_bounds__(F256_THREADS, 1) lbp_face256_kernel(LbpArgs a)
                     const __nv_bfloat16 b = __float2bfloat16_rn(x);
                     reinterpret_cast<uint16_t*>(a.x_out)[idx] = __bfloat16_as_ushort(b);
                     qv = __bfloat162float(b);
+                } else if (x_dtype == RGBD_DT_BF16X3) {
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+                    reinterpret_cast<uint16_t*>(a.x_out)[idx] = __bfloat16_as_ushort(hi);
+                    reinterpret_cast<uint16_t*>(a.x_out)[idx + a.x_plane] = __bfloat16_as_ushort(lo);
+                    qv = __bfloat162float(hi) + __bfloat162float(lo);
                 } else if (x_dtype == RGBD_DT_FP8) {
                     const __nv_fp8_e4m3 b(x * a.x_scale);
                     reinterpret_cast<uint8_t*>(a.x_out)[idx] = b.__x;
@@ -808,11 +832,20 @@ __global__ void crop_affine_kernel(const uint8_t* __restrict__ grey, const uint1
 // ---------------------------------------------------------------------------------------
 // A5 alone: per-cell normalisation of count rows; one CTA per row.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ float store_x(void* out, int dtype, size_t idx, float x, float scale) {
+__device__ __forceinline__ float store_x(void* out, int dtype, size_t idx, float x, float scale,
+                                         size_t plane = 0) {
     if (dtype == RGBD_DT_BF16) {
         const __nv_bfloat16 q = __float2bfloat16_rn(x);
         reinterpret_cast<uint16_t*>(out)[idx] = __bfloat16_as_ushort(q);
         return __bfloat162float(q);
+    } else if (dtype == RGBD_DT_BF16X3) {
+        // hi = bf16(x), lo = bf16(x - hi): x = hi + lo to 2^-18 relative
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        const float hf = __bfloat162float(hi);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(x - hf);
+        reinterpret_cast<uint16_t*>(out)[idx] = __bfloat16_as_ushort(hi);
+        reinterpret_cast<uint16_t*>(out)[idx + plane] = __bfloat16_as_ushort(lo);
+        return hf + __bfloat162float(lo);
     } else if (dtype == RGBD_DT_FP8) {
         const __nv_fp8_e4m3 q(x * scale);
         reinterpret_cast<uint8_t*>(out)[idx] = q.__x;
@@ -824,7 +857,7 @@ __device__ __forceinline__ float store_x(void* out, int dtype, size_t idx, float
 
 __global__ void normalize_kernel(const uint16_t* __restrict__ feats, int n, int dim, int nbins,
                                  int x_dtype, void* x_out, int k_pad, float x_scale, float* xsq,
-                                 float* row_max) {
+                                 float* row_max, size_t plane) {
     extern __shared__ uint32_t nv[];  // [dim / nbins]
     __shared__ float red[2][32];
     const int cells = dim / nbins;
@@ -845,7 +878,7 @@ __global__ void normalize_kernel(const uint16_t* __restrict__ feats, int n, int 
                 x = t ? (float)h[j] / (float)t : 0.f;
             }
             mx = fmaxf(mx, x);
-            const float q = store_x(x_out, x_dtype, (size_t)row * k_pad + j, x, x_scale);
+            const float q = store_x(x_out, x_dtype, (size_t)row * k_pad + j, x, x_scale, plane);
             sq = fmaf(q, q, sq);
         }
         for (int off = 16; off > 0; off >>= 1) {
@@ -950,13 +983,14 @@ int launch_crop_affine(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
 }
 
 int launch_normalize(const uint16_t* feats, int n, int dim, int nbins, int x_dtype, void* x_out,
-                     int k_pad, float x_scale, float* xsq, float* row_max, cudaStream_t s) {
+                     int k_pad, float x_scale, float* xsq, float* row_max, cudaStream_t s, size_t plane) {
     const int cells = dim / nbins;
     const size_t smem = sizeof(uint32_t) * (size_t)cells;
     if (smem > 48 * 1024) return set_error(RGBD_ERR_UNSUPPORTED, "normalize: %d cells", cells);
     const int grid = std::min(n, 8192);
+    if (plane == 0) plane = (size_t)n * k_pad;
     normalize_kernel<<<grid, 256, smem, s>>>(feats, n, dim, nbins, x_dtype, x_out, k_pad, x_scale,
-                                             xsq, row_max);
+                                             xsq, row_max, plane);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "lbp_normalize_features: launch");
     return RGBD_OK;

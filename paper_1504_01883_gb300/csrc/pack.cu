@@ -40,6 +40,22 @@ __global__ void asum_kernel(const float* __restrict__ coef, int C, int n, float*
     if (lane == 0) asum[c] = (float)s;
 }
 
+// asum_tile[t][c] = sum of a_ci over the SVs of tile t (fp64); one warp per (tile, class),
+// zero for the padded classes c >= C.
+__global__ void asum_tile_kernel(const float* __restrict__ coef, int C, int C_pad, int n_pad,
+                                 float* __restrict__ out) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int nt = n_pad / kSvTile;
+    if (w >= nt * C_pad) return;
+    const int t = w / C_pad, c = w - t * C_pad;
+    double s = 0.0;
+    if (c < C)
+        for (int i = lane; i < kSvTile; i += 32) s += (double)coef[(size_t)c * n_pad + t * kSvTile + i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+    if (lane == 0) out[w] = (float)s;
+}
+
 __global__ void copy_pad_rows_kernel(const float* __restrict__ src, int rows, int cols, int ld,
                                      float* __restrict__ dst) {
     const size_t total = (size_t)rows * ld;
@@ -77,6 +93,7 @@ void free_model(rgbd_svm* m) {
     cudaFree(m->coef);
     cudaFree(m->coef_bf16);
     cudaFree(m->asum);
+    cudaFree(m->asum_tile);
     cudaFree(m->bias);
     delete m;
 }
@@ -102,6 +119,7 @@ int encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, u
 
 using namespace rgbd;
 
+// bytes per element of a packed row (RGBD_DT_BF16X3: two bf16 planes)
 static size_t dtype_bytes(int dt) { return dt == RGBD_DT_BF16 ? 2 : (dt == RGBD_DT_FP8 ? 1 : 4); }
 
 extern "C" {
@@ -120,7 +138,8 @@ int svm_train_data_pack(rgbd_ctx* ctx, const uint16_t* sv_feats, int n_sv, int d
     if (kernel == RGBD_KERNEL_RBF) {
         if (!sv_feats || n_sv <= 0) return set_error(RGBD_ERR_ARG, "svm_train_data_pack: RBF needs support vectors");
         if (!(gamma > 0.f)) return set_error(RGBD_ERR_ARG, "svm_train_data_pack: gamma must be > 0");
-        if (dtype != RGBD_DT_F32 && dtype != RGBD_DT_BF16 && dtype != RGBD_DT_FP8 && dtype != RGBD_DT_TF32)
+        if (dtype != RGBD_DT_F32 && dtype != RGBD_DT_BF16 && dtype != RGBD_DT_FP8 && dtype != RGBD_DT_TF32 &&
+            dtype != RGBD_DT_BF16X3)
             return set_error(RGBD_ERR_ARG, "svm_train_data_pack: dtype %d", dtype);
     } else {
         if (!coef) return set_error(RGBD_ERR_ARG, "svm_train_data_pack: a linear model needs coef (w)");
@@ -158,7 +177,7 @@ int svm_train_data_pack(rgbd_ctx* ctx, const uint16_t* sv_feats, int n_sv, int d
         TRY_CUDA(cudaGetLastError(), "pack: w copy");
     } else {
         m->n_sv = n_sv;
-        m->n_pad = (n_sv + 255) / 256 * 256;
+        m->n_pad = (n_sv + kSvTile - 1) / kSvTile * kSvTile;
         const size_t esz = dtype_bytes(dtype);
         TRY_CUDA(cudaMalloc(&m->sv, esz * (size_t)m->n_pad * m->k_pad), "pack: sv");
         TRY_CUDA(cudaMalloc(&m->sv_sq, sizeof(float) * (size_t)m->n_pad), "pack: sv_sq");
@@ -196,7 +215,8 @@ int svm_train_data_pack(rgbd_ctx* ctx, const uint16_t* sv_feats, int n_sv, int d
                 return rc;
             }
         } else {
-            rc = launch_normalize(sv_feats, n_sv, dim, nbins, dtype, m->sv, m->k_pad, 1.f, m->sv_sq, nullptr, s);
+            rc = launch_normalize(sv_feats, n_sv, dim, nbins, dtype, m->sv, m->k_pad, 1.f, m->sv_sq, nullptr, s,
+                                  (size_t)m->n_pad * m->k_pad);
             if (rc) {
                 free_model(m);
                 return rc;
@@ -210,6 +230,10 @@ int svm_train_data_pack(rgbd_ctx* ctx, const uint16_t* sv_feats, int n_sv, int d
             TRY_CUDA(cudaGetLastError(), "pack: coef launch");
             asum_kernel<<<(m->C + 7) / 8, 256, 0, s>>>(coef, m->C, n_sv, m->asum);
             TRY_CUDA(cudaGetLastError(), "pack: asum launch");
+            const int tile_sums = m->n_pad / kSvTile * m->C_pad;
+            TRY_CUDA(cudaMalloc(&m->asum_tile, sizeof(float) * (size_t)tile_sums), "pack: tile sums");
+            asum_tile_kernel<<<(tile_sums + 7) / 8, 256, 0, s>>>(m->coef, m->C, m->C_pad, m->n_pad, m->asum_tile);
+            TRY_CUDA(cudaGetLastError(), "pack: tile sums launch");
         }
     }
     if (coef) {

@@ -255,8 +255,9 @@ __global__ void __launch_bounds__(256, 1) rbf_tiled_kernel(const float* __restri
 // ---------------------------------------------------------------------------------------
 __global__ void reduce_scores_kernel(const float* __restrict__ part, const float* __restrict__ ref,
                                      int splits, int n, int C, int C_stride, const float* __restrict__ asum,
-                                     const float* __restrict__ asum_split, const float* __restrict__ bias,
-                                     float gamma, float* __restrict__ scores, int32_t* __restrict__ labels) {
+                                     const float* __restrict__ asum_tile, int tps, int nt,
+                                     const float* __restrict__ bias, float gamma, float* __restrict__ scores,
+                                     int32_t* __restrict__ labels) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= n) return;
@@ -269,8 +270,11 @@ __global__ void reduce_scores_kernel(const float* __restrict__ part, const float
         for (int s = 0; s < splits; ++s) {
             const float d = part[((size_t)s * n + row) * C_stride + c];
             if (ref) {
+                float as = 0.f;  // sum of a_ci over the SVs of split s
+                if (s > 0)
+                    for (int t = s * tps; t < min(nt, (s + 1) * tps); ++t) as += asum_tile[(size_t)t * C_stride + c];
                 const float delta = (s == 0) ? 0.f : expm1f(-gamma * (ref[(size_t)s * n + row] - rstar));
-                acc += d + delta * (asum_split[(size_t)s * C_stride + c] + d);
+                acc += d + delta * (as + d);
             } else {
                 acc += d;
             }
@@ -298,11 +302,11 @@ __global__ void reduce_scores_kernel(const float* __restrict__ part, const float
 }  // namespace
 
 int launch_reduce_scores(const float* part, const float* ref, int splits, int n, int C, int C_stride,
-                         const float* asum, const float* asum_split, const float* bias, float gamma,
-                         float* scores, int32_t* labels, cudaStream_t s) {
+                         const float* asum, const float* asum_tile, int tiles_per_split, int n_tiles,
+                         const float* bias, float gamma, float* scores, int32_t* labels, cudaStream_t s) {
     const int rows_per_block = 8;
     reduce_scores_kernel<<<(n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(
-        part, ref, splits, n, C, C_stride, asum, asum_split, bias, gamma, scores, labels);
+        part, ref, splits, n, C, C_stride, asum, asum_tile, tiles_per_split, n_tiles, bias, gamma, scores, labels);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "svm_score: reduce launch");
     return RGBD_OK;
@@ -351,7 +355,7 @@ int score_rbf_f32(rgbd_ctx* ctx, const rgbd_svm* m, const float* x, const float*
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_error(e, "svm_score: rbf small-n launch");
         // warps past n_sv wrote zeros (empty SV range), so every split is summed
-        return launch_reduce_scores(part, nullptr, total_warps, n, m->C, m->C, m->asum, nullptr, m->bias,
+        return launch_reduce_scores(part, nullptr, total_warps, n, m->C, m->C, m->asum, nullptr, 0, 0, m->bias,
                                     m->gamma, scores, labels, s);
     }
     static bool attr_set = false;
@@ -375,7 +379,7 @@ int score_rbf_f32(rgbd_ctx* ctx, const rgbd_svm* m, const float* x, const float*
                                              m->coef, m->C, m->gamma, tps, part);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "svm_score: rbf tiled launch");
-    return launch_reduce_scores(part, nullptr, splits, n, m->C, m->C, m->asum, nullptr, m->bias, m->gamma,
+    return launch_reduce_scores(part, nullptr, splits, n, m->C, m->C, m->asum, nullptr, 0, 0, m->bias, m->gamma,
                                 scores, labels, s);
 }
 

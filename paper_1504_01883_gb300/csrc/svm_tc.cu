@@ -35,18 +35,34 @@ namespace rgbd {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 256;
-constexpr int STAGES = 3;
+constexpr int BN = kSvTile;
 constexpr int X_TILE = BM * 128;   // bytes of one X k-block
 constexpr int SV_TILE = BN * 128;  // bytes of one SV k-block
-constexpr int STAGE_BYTES = X_TILE + SV_TILE;
 constexpr int F_CHUNK = BM * 64 * 2;               // one 64-column bf16 chunk of F (16 KB)
-constexpr int F_OFF = STAGES * STAGE_BYTES;        // 2 slots
 constexpr int MAX_CPAD = 128;
 constexpr int COEF_CHUNK_MAX = MAX_CPAD * 64 * 2;  // one 64-SV chunk of a (C_pad rows)
-constexpr int COEF_OFF = F_OFF + 2 * F_CHUNK;      // 2 slots
-constexpr int BAR_OFF = COEF_OFF + 2 * COEF_CHUNK_MAX;
-constexpr int SMEM_BYTES = BAR_OFF + 256 + 1024;   // + barriers + alignment slack
+constexpr int MAX_STAGES = 5;
+
+// Launch modes of the kernel.
+enum { MODE_SINGLE = 0,   // one CTA per (row block, split)
+       MODE_MC = 1,       // CTA pairs; each loads half of every SV k-block and multicasts it
+       MODE_PAIR = 2 };   // CTA pairs run one 256-row MMA (cta_group::2): each CTA holds its own
+                          // 128 X rows and half of the SV tile (and of the coefficient chunk)
+
+// Shared-memory layout of a mode: main ring, F ring (2 slots), coefficient ring (2 slots), barriers.
+template <int MODE>
+struct Lay {
+    static constexpr int STAGES = MODE == MODE_PAIR ? 5 : 3;
+    static constexpr int SV_BYTES = MODE == MODE_PAIR ? SV_TILE / 2 : SV_TILE;  // SV rows per stage
+    static constexpr int STAGE = X_TILE + SV_BYTES;
+    static constexpr int F_OFF = STAGES * STAGE;
+    static constexpr int COEF_CHUNK = MODE == MODE_PAIR ? COEF_CHUNK_MAX / 2 : COEF_CHUNK_MAX;
+    static constexpr int COEF_OFF = F_OFF + 2 * F_CHUNK;
+    static constexpr int BAR_OFF = COEF_OFF + 2 * COEF_CHUNK;
+    static constexpr int SMEM = BAR_OFF + 256 + 1024;  // + barriers + alignment slack
+    static_assert(STAGES <= MAX_STAGES, "barrier slots");
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+};
 constexpr int NUM_WARPS = 11;
 constexpr int NUM_THREADS = NUM_WARPS * 32;
 constexpr uint32_t TMEM_COLS = 512;                // G: 256 columns, D: C_pad columns at 256
@@ -54,9 +70,9 @@ constexpr uint64_t WAIT_NS = 1000000000ull;        // 1 s: far above any legitim
 
 // barrier slots (8 bytes each) inside the barrier block
 enum {
-    B_FULL = 0,                   // STAGES
-    B_EMPTY = B_FULL + STAGES,    // STAGES
-    B_GFULL = B_EMPTY + STAGES,
+    B_FULL = 0,                       // MAX_STAGES
+    B_EMPTY = B_FULL + MAX_STAGES,    // MAX_STAGES
+    B_GFULL = B_EMPTY + MAX_STAGES,
     B_GEMPTY = B_GFULL + 1,
     B_FFULL = B_GEMPTY + 1,       // 2 (F chunk written + its coefficient chunk loaded)
     B_FEMPTY = B_FFULL + 2,       // 2 (second MMA of the chunk done)
@@ -83,6 +99,7 @@ struct TcParams {
     uint32_t idesc_main;
     uint32_t idesc_second;
     int kind;         // 0 = f16 (bf16), 1 = f8f6f4 (e4m3), 2 = tf32
+    int passes;       // 1, or 3 for split bf16 operands (RGBD_DT_BF16X3)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -107,19 +124,30 @@ __device__ __forceinline__ void bar_arrive_tx(uint32_t a, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
+// CL: acquire at cluster scope (the barrier also receives arrivals from the peer CTA).
+template <bool CL = false>
 __device__ __forceinline__ bool bar_try(uint32_t a, uint32_t parity) {
     uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
+    if (CL)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
     return ok != 0;
 }
 // Bounded wait.  Returns false when the CTA is aborting (deadline passed here or elsewhere).
+template <bool CL = false>
 __device__ __noinline__ bool bar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
     const uint64_t t0 = globaltimer();
-    while (!bar_try(a, parity)) {
+    while (!bar_try<CL>(a, parity)) {
         if (*abort_flag) return false;
         if (globaltimer() - t0 > WAIT_NS) {
             *abort_flag = 1;
@@ -160,6 +188,35 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// The address of the same shared-memory object in cluster CTA 0 (the pair's MMA issuer).
+__device__ __forceinline__ uint32_t map_rank0(uint32_t a) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(r) : "r"(a));
+    return r;
+}
+// Arrive on an mbarrier given by its cluster address (possibly in the peer CTA).
+__device__ __forceinline__ void bar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// TMA load into this CTA's shared memory whose completion is counted on an mbarrier of either
+// CTA of the pair (cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                                 uint32_t bar_cluster) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cluster)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit2(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_commit2_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -175,22 +232,42 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;             // 128-byte swizzle
     return d;
 }
+template <int CG>
 __device__ __forceinline__ void mma_issue(int kind, uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    if (kind == 0) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    } else if (kind == 1) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    if (CG == 1) {
+        if (kind == 0) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        } else if (kind == 1) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        } else {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        }
     } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        if (kind == 0) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        } else if (kind == 1) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        } else {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        }
     }
 }
 #define TC_LD_X32(taddr, v)                                                                                   \
@@ -217,21 +294,31 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 // ---------------------------------------------------------------------------------------
 // The kernel
 // ---------------------------------------------------------------------------------------
-// MC: the CTA runs in a cluster of two along the rows.  Both CTAs use the same SV tiles, so each
-// loads half of every SV k-block and multicasts it into both CTAs' stage, and each CTA's MMA
+// MODE_MC: the CTA runs in a cluster of two along the rows.  Both CTAs use the same SV tiles, so
+// each loads half of every SV k-block and multicasts it into both CTAs' stage, and each CTA's MMA
 // releases the stage in both CTAs: the pair reads each SV k-block from L2 once.
-template <bool MC>
+// MODE_PAIR: the two CTAs of a cluster form one 256-row MMA (tcgen05 cta_group::2).  Each CTA
+// loads its own 128 X rows and one half of the SV tile (CTA r: SVs r*128 .. r*128+127 of the
+// tile) and one half of the classes of each coefficient chunk; CTA 0 issues every MMA, which
+// reads the operands of both CTAs and writes G and D into both CTAs' tensor memory (each CTA
+// holds its own rows).  All copies count on CTA 0's barriers, and CTA 0's commits arrive on
+// both CTAs' barriers.  Per MMA each CTA supplies 8 KB of operands instead of 12 KB.
+template <int MODE>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     rbf_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_sv,
-                  const __grid_constant__ CUtensorMap tm_coef, const TcParams p) {
+                  const __grid_constant__ CUtensorMap tm_coef, const __grid_constant__ CUtensorMap tm_x2,
+                  const __grid_constant__ CUtensorMap tm_sv2, const TcParams p) {
+    constexpr bool MC = MODE == MODE_MC, PAIR = MODE == MODE_PAIR;
+    constexpr int CG = PAIR ? 2 : 1;
+    using L = Lay<MODE>;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned for the 128B swizzle atoms
     unsigned char* gbase = smem_raw + (base - raw);
-    const uint32_t bars = base + BAR_OFF;
+    const uint32_t bars = base + L::BAR_OFF;
     auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + BAR_OFF + 8 * B_COUNT);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + BAR_OFF + 8 * B_COUNT + 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + L::BAR_OFF + 8 * B_COUNT);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + L::BAR_OFF + 8 * B_COUNT + 8);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM;
@@ -242,14 +329,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int Q = 4 * U;     // 64-column chunks of this split
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < L::STAGES; ++s) {
             bar_init(bar(B_FULL + s), 1);
             bar_init(bar(B_EMPTY + s), MC ? 2 : 1);  // both CTAs' MMAs read a multicast stage
         }
         bar_init(bar(B_GFULL), 1);
-        bar_init(bar(B_GEMPTY), 8);
+        bar_init(bar(B_GEMPTY), PAIR ? 16 : 8);  // the epilogue warps (of both CTAs of a pair)
         for (int s = 0; s < 2; ++s) {
-            bar_init(bar(B_FFULL + s), 4 + 1);  // 4 epilogue warps + the coefficient producer
+            // 4 epilogue warps (per CTA of a pair) + the coefficient producer
+            bar_init(bar(B_FFULL + s), PAIR ? 8 + 1 : 4 + 1);
             bar_init(bar(B_FEMPTY + s), 1);
         }
         bar_init(bar(B_DFULL), 1);
@@ -258,22 +346,33 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    if (PAIR) cluster_sync();  // both CTAs are running before they allocate together
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (PAIR) {
+            // one warp of each CTA of the pair allocates collectively (same columns in both)
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncwarp();
-    if (MC)
-        cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
+    if (MC || PAIR)
+        cluster_sync();  // the peer's barriers are initialised before any copy or commit reaches them
     else
         __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t crank = MC ? cluster_rank() : 0u;
-    const uint32_t coef_chunk_bytes = (uint32_t)p.C_pad * 128u;
+    const uint32_t crank = (MC || PAIR) ? cluster_rank() : 0u;
+    const uint32_t coef_chunk_bytes = (uint32_t)(PAIR ? p.C_pad / 2 : p.C_pad) * 128u;
 
     if (warp == 0) {
         // ===================== TMA producer: X and SV k-blocks =====================
@@ -285,32 +384,51 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool alive = true;
             for (int u = 0; u < U && alive; ++u) {
                 const int n0 = (t0 + u) * BN;
-                for (int kb = 0; kb < p.k_blocks; ++kb) {
-                    if (!bar_wait(bar(B_EMPTY + stage), phase ^ 1u, abort_flag, p.status)) {
+                for (int kt = 0; kt < p.passes * p.k_blocks; ++kt) {
+                    // three passes for split bf16 operands: (x_hi, sv_hi), (x_hi, sv_lo), (x_lo, sv_hi)
+                    const int pass = kt / p.k_blocks, kb = kt - pass * p.k_blocks;
+                    const CUtensorMap* mx = (pass == 2) ? &tm_x2 : &tm_x;
+                    const CUtensorMap* msv = (pass == 1) ? &tm_sv2 : &tm_sv;
+                    if (!bar_wait<PAIR>(bar(B_EMPTY + stage), phase ^ 1u, abort_flag, p.status)) {
                         alive = false;
                         break;
                     }
-                    const uint32_t sa = base + (uint32_t)stage * STAGE_BYTES;
-                    bar_arrive_tx(bar(B_FULL + stage), STAGE_BYTES);
-                    tma_load_2d(sa, &tm_x, kb * p.k_elems, m0, bar(B_FULL + stage));
-                    if (MC)
-                        tma_load_2d_mc(sa + X_TILE + crank * (SV_TILE / 2), &tm_sv, kb * p.k_elems,
-                                       n0 + (int)crank * (BN / 2), bar(B_FULL + stage), (uint16_t)0x3);
-                    else
-                        tma_load_2d(sa + X_TILE, &tm_sv, kb * p.k_elems, n0, bar(B_FULL + stage));
+                    const uint32_t sa = base + (uint32_t)stage * L::STAGE;
+                    if (PAIR) {
+                        const uint32_t fb = map_rank0(bar(B_FULL + stage));
+                        if (crank == 0) bar_arrive_tx(bar(B_FULL + stage), 2u * L::STAGE);
+                        tma_load_2d_pair(sa, mx, kb * p.k_elems, m0, fb);
+                        tma_load_2d_pair(sa + X_TILE, msv, kb * p.k_elems, n0 + (int)crank * (BN / 2), fb);
+                    } else {
+                        bar_arrive_tx(bar(B_FULL + stage), L::STAGE);
+                        tma_load_2d(sa, mx, kb * p.k_elems, m0, bar(B_FULL + stage));
+                        if (MC)
+                            tma_load_2d_mc(sa + X_TILE + crank * (SV_TILE / 2), msv, kb * p.k_elems,
+                                           n0 + (int)crank * (BN / 2), bar(B_FULL + stage), (uint16_t)0x3);
+                        else
+                            tma_load_2d(sa + X_TILE, msv, kb * p.k_elems, n0, bar(B_FULL + stage));
+                    }
                     armed |= 1u << stage;
                     armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-                    if (++stage == STAGES) {
+                    if (++stage == L::STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
                 }
             }
-            if (!alive) {  // drain: wait (bounded) for the copies this thread issued
+            if (!alive && PAIR && crank != 0) {
+                // this CTA's copies count on the peer's barriers: give those in flight a bounded
+                // 200 us to land
+                (void)armed;
                 const uint64_t tq = globaltimer();
-                for (int s = 0; s < STAGES; ++s)
+                while (globaltimer() - tq < 200000ull) {
+                }
+            } else if (!alive) {  // drain: wait (bounded) for the copies this thread issued
+                const uint64_t tq = globaltimer();
+                for (int s = 0; s < L::STAGES; ++s)
                     if (armed & (1u << s))
-                        while (!bar_try(bar(B_FULL + s), (armed_par >> s) & 1u) && globaltimer() - tq < WAIT_NS) {
+                        while (!bar_try<PAIR>(bar(B_FULL + s), (armed_par >> s) & 1u) &&
+                               globaltimer() - tq < WAIT_NS) {
                         }
             }
         }
@@ -322,13 +440,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool alive = true;
             for (int q = 0; q < Q && alive; ++q) {
                 const int slot = q & 1;
-                if (q >= 2 && !bar_wait(bar(B_FEMPTY + slot), (uint32_t)(((q - 2) >> 1) & 1), abort_flag, p.status)) {
+                if (q >= 2 &&
+                    !bar_wait<PAIR>(bar(B_FEMPTY + slot), (uint32_t)(((q - 2) >> 1) & 1), abort_flag, p.status)) {
                     alive = false;
                     break;
                 }
                 const int n0 = (t0 + (q >> 2)) * BN + (q & 3) * 64;
-                bar_arrive_tx(bar(B_FFULL + slot), coef_chunk_bytes);
-                tma_load_2d(base + COEF_OFF + slot * COEF_CHUNK_MAX, &tm_coef, n0, 0, bar(B_FFULL + slot));
+                const uint32_t dst = base + L::COEF_OFF + slot * L::COEF_CHUNK;
+                if (PAIR) {
+                    if (crank == 0) bar_arrive_tx(bar(B_FFULL + slot), 2u * coef_chunk_bytes);
+                    tma_load_2d_pair(dst, &tm_coef, n0, (int)crank * (p.C_pad / 2), map_rank0(bar(B_FFULL + slot)));
+                } else {
+                    bar_arrive_tx(bar(B_FFULL + slot), coef_chunk_bytes);
+                    tma_load_2d(dst, &tm_coef, n0, 0, bar(B_FFULL + slot));
+                }
                 armed |= 1u << slot;
                 armed_par = (armed_par & ~(1u << slot)) | ((uint32_t)((q >> 1) & 1) << slot);
             }
@@ -342,8 +467,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
         }
     } else if (warp == 1) {
-        // ===================== MMA issuer =====================
-        if (lane == 0) {
+        // ===================== MMA issuer (CTA 0 of a pair) =====================
+        if (lane == 0 && (!PAIR || crank == 0)) {
             int stage = 0;
             uint32_t phase = 0;
             bool alive = true;
@@ -353,22 +478,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             auto service = [&]() -> bool {
                 if (q_next >= q_avail) return false;
                 const int slot = q_next & 1;
-                if (!bar_try(bar(B_FFULL + slot), (uint32_t)((q_next >> 1) & 1))) return false;
+                if (!bar_try<PAIR>(bar(B_FFULL + slot), (uint32_t)((q_next >> 1) & 1))) return false;
                 tc_fence_after();
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
-                    const uint64_t a = sdesc(base + F_OFF + slot * F_CHUNK + ks * 32);
-                    const uint64_t b = sdesc(base + COEF_OFF + slot * COEF_CHUNK_MAX + ks * 32);
-                    mma_issue(0, d_tmem, a, b, p.idesc_second, (q_next > 0 || ks > 0) ? 1u : 0u);
+                    const uint64_t a = sdesc(base + L::F_OFF + slot * F_CHUNK + ks * 32);
+                    const uint64_t b = sdesc(base + L::COEF_OFF + slot * L::COEF_CHUNK + ks * 32);
+                    mma_issue<CG>(0, d_tmem, a, b, p.idesc_second, (q_next > 0 || ks > 0) ? 1u : 0u);
                 }
-                tc_commit(bar(B_FEMPTY + slot));
+                if (PAIR)
+                    tc_commit2_mc(bar(B_FEMPTY + slot), (uint16_t)0x3);
+                else
+                    tc_commit(bar(B_FEMPTY + slot));
                 ++q_next;
                 return true;
             };
             // Blocks (bounded) until barrier (a, parity) completes, servicing chunks meanwhile.
             auto wait_servicing = [&](uint32_t a, uint32_t parity) -> bool {
                 const uint64_t tw = globaltimer();
-                while (!bar_try(a, parity)) {
+                while (!bar_try<PAIR>(a, parity)) {
                     if (service()) continue;
                     if (*abort_flag) return false;
                     if (globaltimer() - tw > WAIT_NS) {
@@ -387,31 +515,36 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                     tc_fence_after();
                 }
-                for (int kb = 0; kb < p.k_blocks; ++kb) {
+                for (int kt = 0; kt < p.passes * p.k_blocks; ++kt) {
                     if (!wait_servicing(bar(B_FULL + stage), phase)) {
                         alive = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = base + (uint32_t)stage * STAGE_BYTES;
+                    const uint32_t sa = base + (uint32_t)stage * L::STAGE;
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
                         const uint64_t a = sdesc(sa + ks * 32);
                         const uint64_t bd = sdesc(sa + X_TILE + ks * 32);
-                        mma_issue(p.kind, tmem, a, bd, p.idesc_main, (kb > 0 || ks > 0) ? 1u : 0u);
+                        mma_issue<CG>(p.kind, tmem, a, bd, p.idesc_main, (kt > 0 || ks > 0) ? 1u : 0u);
                     }
-                    if (MC)
+                    if (PAIR)
+                        tc_commit2_mc(bar(B_EMPTY + stage), (uint16_t)0x3);
+                    else if (MC)
                         tc_commit_mc(bar(B_EMPTY + stage), (uint16_t)0x3);
                     else
                         tc_commit(bar(B_EMPTY + stage));
-                    if (++stage == STAGES) {
+                    if (++stage == L::STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
                     service();
                 }
                 if (!alive) break;
-                tc_commit(bar(B_GFULL));
+                if (PAIR)
+                    tc_commit2_mc(bar(B_GFULL), (uint16_t)0x3);
+                else
+                    tc_commit(bar(B_GFULL));
                 q_avail = 4 * (u + 1);
             }
             // the chunks of the last tile
@@ -426,9 +559,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                 }
             }
-            if (alive) tc_commit(bar(B_DFULL));
+            if (alive) {
+                if (PAIR)
+                    tc_commit2_mc(bar(B_DFULL), (uint16_t)0x3);
+                else
+                    tc_commit(bar(B_DFULL));
+            }
             // drain: every MMA this thread issued has completed once B_DRAIN flips
-            tc_commit(bar(B_DRAIN));
+            if (PAIR)
+                tc_commit2(bar(B_DRAIN));
+            else
+                tc_commit(bar(B_DRAIN));
             const uint64_t tq = globaltimer();
             while (!bar_try(bar(B_DRAIN), 0)) {
                 if (globaltimer() - tq > WAIT_NS) break;
@@ -448,7 +589,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         bool alive = true;
         auto wait_warp = [&](uint32_t a, uint32_t parity) -> bool {
             bool ok = false;
-            if (lane == 0) ok = bar_wait(a, parity, abort_flag, p.status);
+            if (lane == 0) ok = bar_wait<PAIR>(a, parity, abort_flag, p.status);
             return __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
         };
         for (int u = 0; u < U && alive; ++u) {
@@ -507,21 +648,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 if (h == 1) {  // this set's last read of G for the tile
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) bar_arrive(bar(B_GEMPTY));
+                    if (lane == 0) {
+                        if (PAIR)
+                            bar_arrive_cluster(map_rank0(bar(B_GEMPTY)));
+                        else
+                            bar_arrive(bar(B_GEMPTY));
+                    }
                 }
                 // the slot is free once the second MMA of chunk q - 2 is done
                 if (q >= 2 && !wait_warp(bar(B_FEMPTY + set), (uint32_t)(((q - 2) >> 1) & 1))) {
                     alive = false;
                     break;
                 }
-                unsigned char* rowp = gbase + F_OFF + set * F_CHUNK + (row >> 3) * 1024 + (row & 7) * 128;
+                unsigned char* rowp = gbase + L::F_OFF + set * F_CHUNK + (row >> 3) * 1024 + (row & 7) * 128;
 #pragma unroll
                 for (int g = 0; g < 8; ++g)
                     *reinterpret_cast<uint4*>(rowp + ((g ^ (row & 7)) << 4)) =
                         make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) bar_arrive(bar(B_FFULL + set));
+                if (lane == 0) {
+                    if (PAIR)
+                        bar_arrive_cluster(map_rank0(bar(B_FFULL + set)));
+                    else
+                        bar_arrive(bar(B_FFULL + set));
+                }
             }
         }
         if (alive && set == 0 && wait_warp(bar(B_DFULL), 0)) {
@@ -544,27 +695,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
     tc_fence_before();
     __syncwarp();
-    if (MC)
+    if (MC || PAIR)
         cluster_sync();  // no CTA leaves while its peer may still multicast into it or arrive on it
     else
         __syncthreads();
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-    }
-}
-
-// asum_split[s][c] = sum of a_ci over the SVs of split s (fp64 accumulation).
-__global__ void asum_split_kernel(const float* __restrict__ coef, int C, int C_pad, int n_pad, int n_sv,
-                                  int sv_per_split, float* __restrict__ out) {
-    const int s = blockIdx.x;
-    const int i0 = s * sv_per_split, i1 = min(n_sv, i0 + sv_per_split);
-    for (int c = threadIdx.x; c < C_pad; c += blockDim.x) {
-        double acc = 0.0;
-        if (c < C)
-            for (int i = i0; i < i1; ++i) acc += (double)coef[(size_t)c * n_pad + i];
-        out[(size_t)s * C_pad + c] = (float)acc;
+        if (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                         : "memory");
     }
 }
 
@@ -620,8 +763,21 @@ int pack_model_tensor_maps(rgbd_svm* m) {
     rc = encode_tmap_2d(&m->tm_sv_half, dt, m->sv, (uint64_t)m->k_pad, (uint64_t)m->n_pad,
                         (uint64_t)m->k_pad * esz, 128u / esz, BN / 2, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
+    // split bf16: the lo plane follows the hi plane (defaults to the hi maps otherwise)
+    const void* lo = m->sv;
+    if (m->dtype == RGBD_DT_BF16X3) lo = reinterpret_cast<const uint16_t*>(m->sv) + (size_t)m->n_pad * m->k_pad;
+    rc = encode_tmap_2d(&m->tm_sv_lo, dt, lo, (uint64_t)m->k_pad, (uint64_t)m->n_pad, (uint64_t)m->k_pad * esz,
+                        128u / esz, BN, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    rc = encode_tmap_2d(&m->tm_sv_lo_half, dt, lo, (uint64_t)m->k_pad, (uint64_t)m->n_pad, (uint64_t)m->k_pad * esz,
+                        128u / esz, BN / 2, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
     rc = encode_tmap_2d(&m->tm_coef, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m->coef_bf16, (uint64_t)m->n_pad,
                         (uint64_t)m->C_pad, (uint64_t)m->n_pad * 2, 64u, (uint32_t)m->C_pad,
+                        CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    rc = encode_tmap_2d(&m->tm_coef_half, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m->coef_bf16, (uint64_t)m->n_pad,
+                        (uint64_t)m->C_pad, (uint64_t)m->n_pad * 2, 64u, (uint32_t)m->C_pad / 2,
                         CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
     m->has_tmaps = true;
@@ -631,10 +787,10 @@ int pack_model_tensor_maps(rgbd_svm* m) {
 namespace {
 
 struct TcPlan {
-    int esz, kind, splits, tps, mt, nt;
+    int esz, kind, passes, splits, tps, mt, nt;
     uint32_t fmt;
     CUtensorMapDataType dt;
-    size_t off_ref, off_as, bytes;
+    size_t off_ref, bytes;
 };
 
 int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
@@ -657,6 +813,7 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
         pl->fmt = 2;  // TF32
         pl->dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     }
+    pl->passes = (m->dtype == RGBD_DT_BF16X3) ? 3 : 1;
     pl->mt = (n + BM - 1) / BM;
     pl->nt = m->n_pad / BN;
     pl->splits = ctx->tune_tc_splits > 0 ? std::min(ctx->tune_tc_splits, pl->nt)
@@ -665,10 +822,8 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
     pl->splits = (pl->nt + pl->tps - 1) / pl->tps;  // every split non-empty
     const size_t part_bytes = sizeof(float) * (size_t)pl->splits * n * m->C_pad;
     const size_t ref_bytes = sizeof(float) * (size_t)pl->splits * n;
-    const size_t as_bytes = sizeof(float) * (size_t)pl->splits * m->C_pad;
     pl->off_ref = (part_bytes + 255) & ~size_t(255);
-    pl->off_as = (pl->off_ref + ref_bytes + 255) & ~size_t(255);
-    pl->bytes = pl->off_as + as_bytes;
+    pl->bytes = pl->off_ref + ref_bytes;
     return RGBD_OK;
 }
 
@@ -676,18 +831,22 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
               float* scores, int32_t* labels, cudaStream_t s, const TcPlan& pl, char* ws) {
     float* part = (float*)ws;
     float* ref = (float*)(ws + pl.off_ref);
-    float* asplit = (float*)(ws + pl.off_as);
-    CUtensorMap tm_x;
+    CUtensorMap tm_x, tm_x2;
     int rc = encode_tmap_2d(&tm_x, pl.dt, x, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * pl.esz,
                             128u / pl.esz, BM, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
-    // pairs of 128-row blocks share their SV tiles, unless tuned off
-    const bool mc = pl.mt >= 2 && ctx->tune_tc_multicast != 2;
-    cudaError_t e = mc ? cudaFuncSetAttribute(rbf_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              SMEM_BYTES)
-                       : cudaFuncSetAttribute(rbf_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              SMEM_BYTES);
-    if (e != cudaSuccess) return cuda_error(e, "svm_score: tc smem attribute");
+    const void* x_lo = x;  // split bf16: the lo plane of the rows follows their hi plane
+    if (pl.passes == 3) x_lo = reinterpret_cast<const uint16_t*>(x) + (size_t)n * m->k_pad;
+    rc = encode_tmap_2d(&tm_x2, pl.dt, x_lo, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * pl.esz,
+                        128u / pl.esz, BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    // Mode: tuning value 1 = multicast pairs, 2 = single CTAs, 3 = 2-CTA MMA pairs, 0 = auto (the
+    // 2-CTA pairs).  Pairs need at least two 128-row blocks.
+    int mode = MODE_SINGLE;
+    if (pl.mt >= 2) {
+        const int t = ctx->tune_tc_multicast;
+        mode = (t == 1) ? MODE_MC : (t == 2) ? MODE_SINGLE : MODE_PAIR;
+    }
     TcParams p;
     p.n = n;
     p.n_sv = m->n_sv;
@@ -704,17 +863,31 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     p.part = part;
     p.ref = ref;
     p.status = ctx->d_status;
-    p.idesc_main = make_idesc(pl.fmt, pl.fmt, BM, BN);
-    p.idesc_second = make_idesc(1, 1, BM, m->C_pad);
+    const int mma_m = mode == MODE_PAIR ? 2 * BM : BM;  // a pair's MMA covers both CTAs' rows
+    p.idesc_main = make_idesc(pl.fmt, pl.fmt, mma_m, BN);
+    p.idesc_second = make_idesc(1, 1, mma_m, m->C_pad);
     p.kind = pl.kind;
-    asum_split_kernel<<<pl.splits, 128, 0, s>>>(m->coef, m->C, m->C_pad, m->n_pad, m->n_sv, pl.tps * BN, asplit);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "svm_score: asum split launch");
-    if (mc) {
+    p.passes = pl.passes;
+    cudaError_t e;
+    if (mode == MODE_SINGLE) {
+        e = cudaFuncSetAttribute(rbf_tc_kernel<MODE_SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Lay<MODE_SINGLE>::SMEM);
+        if (e != cudaSuccess) return cuda_error(e, "svm_score: tc smem attribute");
+        dim3 grid(pl.mt, pl.splits);
+        rbf_tc_kernel<MODE_SINGLE><<<grid, NUM_THREADS, Lay<MODE_SINGLE>::SMEM, s>>>(tm_x, m->tm_sv, m->tm_coef,
+                                                                                     tm_x2, m->tm_sv_lo, p);
+        e = cudaGetLastError();
+    } else {
+        const int smem = mode == MODE_MC ? Lay<MODE_MC>::SMEM : Lay<MODE_PAIR>::SMEM;
+        e = mode == MODE_MC ? cudaFuncSetAttribute(rbf_tc_kernel<MODE_MC>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                            : cudaFuncSetAttribute(rbf_tc_kernel<MODE_PAIR>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return cuda_error(e, "svm_score: tc smem attribute");
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)((pl.mt + 1) / 2 * 2), (unsigned)pl.splits, 1);
         cfg.blockDim = dim3(NUM_THREADS, 1, 1);
-        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cfg.dynamicSmemBytes = smem;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -723,15 +896,16 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, rbf_tc_kernel<true>, tm_x, m->tm_sv_half, m->tm_coef, p);
-    } else {
-        dim3 grid(pl.mt, pl.splits);
-        rbf_tc_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm_x, m->tm_sv, m->tm_coef, p);
-        e = cudaGetLastError();
+        if (mode == MODE_MC)
+            e = cudaLaunchKernelEx(&cfg, rbf_tc_kernel<MODE_MC>, tm_x, m->tm_sv_half, m->tm_coef, tm_x2,
+                                   m->tm_sv_lo_half, p);
+        else
+            e = cudaLaunchKernelEx(&cfg, rbf_tc_kernel<MODE_PAIR>, tm_x, m->tm_sv_half, m->tm_coef_half, tm_x2,
+                                   m->tm_sv_lo_half, p);
     }
     if (e != cudaSuccess) return cuda_error(e, "svm_score: tc launch");
-    return launch_reduce_scores(part, ref, pl.splits, n, m->C, m->C_pad, m->asum, asplit, m->bias, m->gamma, scores,
-                                labels, s);
+    return launch_reduce_scores(part, ref, pl.splits, n, m->C, m->C_pad, m->asum, m->asum_tile, pl.tps, pl.nt,
+                                m->bias, m->gamma, scores, labels, s);
 }
 
 }  // namespace

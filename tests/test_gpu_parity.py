@@ -154,6 +154,16 @@ def test_quantised_rows_bit_exact(B, ctx, orc):
     # the same rows from stored counts (lbp_normalize_features)
     xn, _ = B.lbp_normalize_features(ctx, dev_u16(want), "bf16")
     assert (xn.view(torch.int16).cpu().numpy().view(np.uint16)[:, :dim] == orc.f32_to_bf16(x32)).all()
+    # split bf16: hi = bf16(x), lo = bf16(x - hi) in fp32
+    hi = orc.f32_to_bf16(x32)
+    hi_f = (hi.astype(np.uint32) << 16).view(np.float32)
+    lo = orc.f32_to_bf16((x32 - hi_f).astype(np.float32))
+    for xs in [B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=128, feats=False,
+                                    x_dtype="bf16x3")[1],
+               B.lbp_normalize_features(ctx, dev_u16(want), "bf16x3")[0]]:
+        planes = xs.view(torch.int16).cpu().numpy().view(np.uint16)
+        assert planes.shape[0] == 2
+        assert (planes[0][:, :dim] == hi).all() and (planes[1][:, :dim] == lo).all()
 
 
 def test_normalize_poisson_counts(B, ctx, orc):
@@ -202,7 +212,7 @@ def test_rbf_f32_paths(B, ctx, orc, n, n_sv, C):
     assert agree >= 0.99, agree
 
 
-@pytest.mark.parametrize("dt", ["bf16", "tf32", "fp8"])
+@pytest.mark.parametrize("dt", ["bf16", "tf32", "fp8", "bf16x3"])
 @pytest.mark.parametrize("n,n_sv,C", [(300, 700, 10), (100, 3000, 64), (5, 256, 16)])
 def test_rbf_tensor_core_paths(B, ctx, orc, dt, n, n_sv, C):
     X, SV, a, b, gamma = _scoring_problem(n * 11 + n_sv, n, n_sv, C)
@@ -213,12 +223,35 @@ def test_rbf_tensor_core_paths(B, ctx, orc, dt, n, n_sv, C):
     x64, sv64 = orc.normalize_f64(X), orc.normalize_f64(SV)
     ref = orc.svm_rbf(x64, sv64, a, b, gamma)
     err = rel_score_error(s.cpu().numpy(), ref, rbf_error_scale(x64, sv64, a, b, gamma))
-    bound = {"tf32": 2e-5, "bf16": 5e-5, "fp8": 1e-3}[dt]
+    bound = {"tf32": 2e-5, "bf16": 5e-5, "fp8": 1e-3, "bf16x3": 2e-6}[dt]
     print(f"{dt} n={n} n_sv={n_sv} C={C}: rel err {err:.3e}")
     assert err <= bound, err
 
 
-@pytest.mark.parametrize("splits,mc", [(1, 2), (3, 1), (8, 2)])
+@pytest.mark.parametrize("mc", [3, 1, 2])
+@pytest.mark.parametrize("dt", ["bf16", "fp8", "tf32", "bf16x3"])
+def test_tensor_core_pairing_modes(B, ctx, orc, dt, mc):
+    """Each CTA pairing of the tensor-core kernel (2-CTA MMA pairs, multicast pairs, single CTAs)
+    against the fp64 oracle: 3 row blocks (so one padded CTA in a pair), 600 SVs (a ragged third
+    SV tile), 100 classes (112 padded, 56 per CTA of a pair)."""
+    X, SV, a, b, gamma = _scoring_problem(77 + mc, 300, 600, 100)
+    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype=dt)
+    x, q = B.lbp_normalize_features(ctx, dev_u16(X), dt, x_scale=448.0)
+    ctx.set_tuning(B.TUNE_TC_MULTICAST, mc)
+    try:
+        s, lab = B.svm_score(ctx, model, x, q, x_scale=448.0)
+        assert ctx.status() == 0
+    finally:
+        ctx.set_tuning(B.TUNE_TC_MULTICAST, 0)
+    x64, sv64 = orc.normalize_f64(X), orc.normalize_f64(SV)
+    ref = orc.svm_rbf(x64, sv64, a, b, gamma)
+    err = rel_score_error(s.cpu().numpy(), ref, rbf_error_scale(x64, sv64, a, b, gamma))
+    bound = {"tf32": 2e-5, "bf16": 5e-5, "fp8": 1e-3, "bf16x3": 2e-6}[dt]
+    print(f"{dt} pairing {mc}: rel err {err:.3e}")
+    assert err <= bound, err
+
+
+@pytest.mark.parametrize("splits,mc", [(1, 2), (3, 1), (8, 2), (2, 3), (8, 3)])
 def test_tuning_changes_layout_not_results(B, ctx, orc, splits, mc):
     """Forced SV splits / multicast (the autotuner's knobs) keep the scores within tolerance."""
     X, SV, a, b, gamma = _scoring_problem(5, 300, 2000, 16)
