@@ -189,9 +189,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--score-dtype", default="bf16", choices=["bf16", "tf32", "fp8", "f32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tune", default=None, metavar="CTAS,SPLITS,MC",
-                    help="fixed launch layout (K1 CTAs/SM, scoring splits, multicast 1=on 2=off) instead of "
-                         "the autotuner, e.g. to profile the layout a previous run chose")
+    ap.add_argument("--tune", default=None, metavar="CTAS,SPLITS,PAIRING",
+                    help="fixed launch layout (K1 CTAs/SM, scoring splits, CTA pairing 1=multicast 2=none "
+                         "3=2-CTA MMA) instead of the autotuner, e.g. to profile the layout a previous run chose")
     ap.add_argument("--ref-crops-per-step", type=int, default=8)
     ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision"],
                     help="batch: the headline line; the others measure the remaining workloads")

@@ -4,16 +4,18 @@
 //
 // One CTA (11 warps) owns 128 feature rows and a contiguous range ("split") of 256-wide SV tiles:
 //   warp 0      TMA producer of the main ring: per k-block (128 B of K per row, 128B-swizzled)
-//               the 128-row X block and the 256-row SV block, 3 stages of 48 KB.
-//   warp 1      TMEM owner and MMA issuer (one thread):
+//               the 128-row X block and the SV block (4 stages of 48 KB; 6 of 32 KB in 2-CTA pairs,
+//               where each CTA holds half of the SV tile).
+//   warp 1      TMEM owner and MMA issuer (one thread; in 2-CTA pairs only CTA 0's):
 //                 G (128 x 256 fp32, TMEM)  = X . SV_t^T over all k-blocks   (N = 256 MMAs)
-//                 D (128 x C_pad fp32, TMEM) += F_q . a_q^T  for every 64-column chunk q of F
+//                 D (128 x C_pad fp32, TMEM) += F_q . a_q^T  for every 64-column chunk q of F,
+//               with F read from tensor memory (A operand) and a from shared memory.
 //   warp 2      TMA producer of the bf16 coefficient chunks a[c][64 SVs] (2-slot ring).
 //   warps 3-10  epilogue, two sets of four warps (one per TMEM lane quarter); set k handles the
 //               64-column chunks k and k + 2 of every tile.  One thread per row reads G with
 //               tcgen05.ld, forms d^2 = |x|^2 + |sv|^2 - 2 G and F = expm1(-gamma (d^2 - r)) in
-//               bf16, and writes F into its slot of a 2-slot ring in the UMMA K-major 128B-swizzle
-//               layout, which the second MMA reads.  r is the row's mean d^2 over chunks 0
+//               bf16, and stores F with tcgen05.st into its slot (two slots of 32 packed columns)
+//               for the second MMA.  r is the row's mean d^2 over chunks 0
 //               and 2 of the split's first tile; since exp(-gamma d^2) = exp(-gamma r) (1 + F),
 //                 S_c = sum_splits exp(-gamma r_s) (sum_{i in s} a_ci + D_s[c]) + b_c,
 //               and F keeps the small per-SV variation at full relative precision (gamma d^2 is
@@ -38,10 +40,9 @@ constexpr int BM = 128;
 constexpr int BN = kSvTile;
 constexpr int X_TILE = BM * 128;   // bytes of one X k-block
 constexpr int SV_TILE = BN * 128;  // bytes of one SV k-block
-constexpr int F_CHUNK = BM * 64 * 2;               // one 64-column bf16 chunk of F (16 KB)
 constexpr int MAX_CPAD = 128;
 constexpr int COEF_CHUNK_MAX = MAX_CPAD * 64 * 2;  // one 64-SV chunk of a (C_pad rows)
-constexpr int MAX_STAGES = 5;
+constexpr int MAX_STAGES = 6;
 
 // Launch modes of the kernel.
 enum { MODE_SINGLE = 0,   // one CTA per (row block, split)
@@ -49,15 +50,15 @@ enum { MODE_SINGLE = 0,   // one CTA per (row block, split)
        MODE_PAIR = 2 };   // CTA pairs run one 256-row MMA (cta_group::2): each CTA holds its own
                           // 128 X rows and half of the SV tile (and of the coefficient chunk)
 
-// Shared-memory layout of a mode: main ring, F ring (2 slots), coefficient ring (2 slots), barriers.
+// Shared-memory layout of a mode: main ring, coefficient ring (2 slots), barriers.  (The F
+// operand of the second MMA lives in tensor memory.)
 template <int MODE>
 struct Lay {
-    static constexpr int STAGES = MODE == MODE_PAIR ? 5 : 3;
+    static constexpr int STAGES = MODE == MODE_PAIR ? 6 : 4;
     static constexpr int SV_BYTES = MODE == MODE_PAIR ? SV_TILE / 2 : SV_TILE;  // SV rows per stage
     static constexpr int STAGE = X_TILE + SV_BYTES;
-    static constexpr int F_OFF = STAGES * STAGE;
     static constexpr int COEF_CHUNK = MODE == MODE_PAIR ? COEF_CHUNK_MAX / 2 : COEF_CHUNK_MAX;
-    static constexpr int COEF_OFF = F_OFF + 2 * F_CHUNK;
+    static constexpr int COEF_OFF = STAGES * STAGE;
     static constexpr int BAR_OFF = COEF_OFF + 2 * COEF_CHUNK;
     static constexpr int SMEM = BAR_OFF + 256 + 1024;  // + barriers + alignment slack
     static_assert(STAGES <= MAX_STAGES, "barrier slots");
@@ -65,7 +66,11 @@ struct Lay {
 };
 constexpr int NUM_WARPS = 11;
 constexpr int NUM_THREADS = NUM_WARPS * 32;
-constexpr uint32_t TMEM_COLS = 512;                // G: 256 columns, D: C_pad columns at 256
+// Tensor memory: G at column 0 (256 columns), D at 256 (C_pad <= 128 columns), the two F slots
+// (128 rows x 64 bf16, packed in pairs: 32 columns each) at 384 and 416.
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TMEM_D = 256;
+constexpr uint32_t TMEM_F = 384;
 constexpr uint64_t WAIT_NS = 1000000000ull;        // 1 s: far above any legitimate wait
 
 // barrier slots (8 bytes each) inside the barrier block
@@ -143,19 +148,42 @@ __device__ __forceinline__ bool bar_try(uint32_t a, uint32_t parity) {
             : "memory");
     return ok != 0;
 }
+// Non-blocking test of a phase (try_wait may suspend the thread for a while when the phase is
+// not complete, which must not happen to the MMA issuer between its k-blocks).
+template <bool CL = false>
+__device__ __forceinline__ bool bar_test(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    if (CL)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+    return ok != 0;
+}
 // Bounded wait.  Returns false when the CTA is aborting (deadline passed here or elsewhere).
+// The deadline clock (%globaltimer, slow to read) is consulted only after a failed test and then
+// once every 16 further tests, so that it never sits on the critical path of a k-block handshake.
 template <bool CL = false>
 __device__ __noinline__ bool bar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+    if (bar_try<CL>(a, parity)) return true;
     const uint64_t t0 = globaltimer();
-    while (!bar_try<CL>(a, parity)) {
+    for (uint32_t it = 1;; ++it) {
+        if (bar_try<CL>(a, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > WAIT_NS) {
+        if ((it & 15u) == 0 && globaltimer() - t0 > WAIT_NS) {
             *abort_flag = 1;
             atomicOr(status, RGBD_STATUS_WAIT_TIMEOUT);
             return false;
         }
     }
-    return true;
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
     asm volatile(
@@ -270,6 +298,30 @@ __device__ __forceinline__ void mma_issue(int kind, uint32_t d, uint64_t a, uint
         }
     }
 }
+// D (+)= A B^T with A (bf16, 128 rows per CTA) in tensor memory and B in shared memory.
+template <int CG>
+__device__ __forceinline__ void mma_issue_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (CG == 1)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+#define TC_ST_X32(taddr, v)                                                                                   \
+    asm volatile(                                                                                             \
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"   \
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),                 \
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),      \
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),         \
+        "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),        \
+        "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])                     \
+        : "memory")
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 #define TC_LD_X32(taddr, v)                                                                                   \
     asm volatile(                                                                                             \
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"     \
@@ -382,9 +434,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int stage = 0;
             uint32_t phase = 0, armed = 0, armed_par = 0;
             bool alive = true;
+            const int KT = p.passes * p.k_blocks;  // k-blocks per tile
             for (int u = 0; u < U && alive; ++u) {
                 const int n0 = (t0 + u) * BN;
-                for (int kt = 0; kt < p.passes * p.k_blocks; ++kt) {
+                for (int kt = 0; kt < KT; ++kt) {
                     // three passes for split bf16 operands: (x_hi, sv_hi), (x_hi, sv_lo), (x_lo, sv_hi)
                     const int pass = kt / p.k_blocks, kb = kt - pass * p.k_blocks;
                     const CUtensorMap* mx = (pass == 2) ? &tm_x2 : &tm_x;
@@ -473,18 +526,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             uint32_t phase = 0;
             bool alive = true;
             int q_next = 0, q_avail = 0;
-            const uint32_t d_tmem = tmem + 256;  // second-MMA accumulator, C_pad columns
+            const uint32_t d_tmem = tmem + TMEM_D;  // second-MMA accumulator, C_pad columns
             // Issues the second MMA of the next finished F chunk; returns false if none is ready.
             auto service = [&]() -> bool {
                 if (q_next >= q_avail) return false;
                 const int slot = q_next & 1;
-                if (!bar_try<PAIR>(bar(B_FFULL + slot), (uint32_t)((q_next >> 1) & 1))) return false;
+                if (!bar_test<PAIR>(bar(B_FFULL + slot), (uint32_t)((q_next >> 1) & 1))) return false;
                 tc_fence_after();
 #pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
-                    const uint64_t a = sdesc(base + L::F_OFF + slot * F_CHUNK + ks * 32);
+                for (int ks = 0; ks < 4; ++ks) {  // K = 16 per MMA: 8 packed columns of F
+                    const uint32_t a = tmem + TMEM_F + 32u * slot + 8u * ks;
                     const uint64_t b = sdesc(base + L::COEF_OFF + slot * L::COEF_CHUNK + ks * 32);
-                    mma_issue<CG>(0, d_tmem, a, b, p.idesc_second, (q_next > 0 || ks > 0) ? 1u : 0u);
+                    mma_issue_ts<CG>(d_tmem, a, b, p.idesc_second, (q_next > 0 || ks > 0) ? 1u : 0u);
                 }
                 if (PAIR)
                     tc_commit2_mc(bar(B_FEMPTY + slot), (uint16_t)0x3);
@@ -493,12 +546,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 ++q_next;
                 return true;
             };
-            // Blocks (bounded) until barrier (a, parity) completes, servicing chunks meanwhile.
+            // Blocks (bounded) until barrier (a, parity) completes, servicing chunks meanwhile:
+            // while a chunk may still arrive the barrier is polled without suspending.
             auto wait_servicing = [&](uint32_t a, uint32_t parity) -> bool {
-                const uint64_t tw = globaltimer();
-                while (!bar_try<PAIR>(a, parity)) {
+                uint64_t tw = 0;
+                for (uint32_t it = 0; !(q_next < q_avail ? bar_test<PAIR>(a, parity) : bar_try<PAIR>(a, parity)); ++it) {
                     if (service()) continue;
                     if (*abort_flag) return false;
+                    if ((it & 15u) != 0) continue;  // the deadline clock is slow to read
+                    if (tw == 0) tw = globaltimer();
                     if (globaltimer() - tw > WAIT_NS) {
                         *abort_flag = 1;
                         atomicOr(p.status, RGBD_STATUS_WAIT_TIMEOUT);
@@ -516,11 +572,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     tc_fence_after();
                 }
                 for (int kt = 0; kt < p.passes * p.k_blocks; ++kt) {
-                    if (!wait_servicing(bar(B_FULL + stage), phase)) {
+                    // The issue loop must stay well under the 512 tensor-pipe cycles of a k-block,
+                    // so the ready case costs one barrier test, the stage's TMA data needs no
+                    // tcgen05 fence (the barrier orders it), and finished F chunks are serviced only
+                    // every 8 k-blocks (the epilogue waits two chunks back).
+                    if (!bar_try<PAIR>(bar(B_FULL + stage), phase) && !wait_servicing(bar(B_FULL + stage), phase)) {
                         alive = false;
                         break;
                     }
-                    tc_fence_after();
                     const uint32_t sa = base + (uint32_t)stage * L::STAGE;
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
@@ -538,7 +597,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         stage = 0;
                         phase ^= 1u;
                     }
-                    service();
+                    if ((kt & 7) == 7) service();
                 }
                 if (!alive) break;
                 if (PAIR)
@@ -660,12 +719,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     alive = false;
                     break;
                 }
-                unsigned char* rowp = gbase + L::F_OFF + set * F_CHUNK + (row >> 3) * 1024 + (row & 7) * 128;
-#pragma unroll
-                for (int g = 0; g < 8; ++g)
-                    *reinterpret_cast<uint4*>(rowp + ((g ^ (row & 7)) << 4)) =
-                        make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                // F of this warp's 32 rows into the slot's 32 columns (row = TMEM lane)
+                TC_ST_X32(tmem + lane_addr + TMEM_F + 32u * (uint32_t)set, pk);
+                tc_wait_st();
+                tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
                     if (PAIR)
@@ -677,7 +734,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         if (alive && set == 0 && wait_warp(bar(B_DFULL), 0)) {
             tc_fence_after();
-            const uint32_t d_tmem = tmem + lane_addr + 256;
+            const uint32_t d_tmem = tmem + lane_addr + TMEM_D;
             float* prow = p.part + ((size_t)split * p.n + grow) * p.C_pad;
 #pragma unroll 1
             for (int c0 = 0; c0 < p.C_pad; c0 += 16) {
