@@ -295,6 +295,17 @@ int rgbd_track_nearest(rgbd_ctx* ctx, const rgbd_rect* prev, int n_prev, const r
 int svm_score_noalloc(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* xsq, int n,
                       float x_scale, float* scores, int32_t* labels, void* stream);
 
+/* ======================================================================================= */
+/* Diagnostics                                                                              */
+/* ======================================================================================= */
+
+/* rgbd_debug_expm1 -- evaluates, for a test, the e^z - 1 the tensor-core RBF epilogue uses
+ * (Section 2.5's kernel value relative to a reference distance, where |z| is small): a
+ * degree-6 Taylor polynomial for |z| < 2^-5, expm1f otherwise.
+ *   z, out   device fp32 [n] (caller-owned); out[i] = e^z[i] - 1.
+ *   Asynchronous on stream.  Errors: RGBD_ERR_ARG for n < 0 or NULL pointers with n > 0. */
+int rgbd_debug_expm1(const float* z, float* out, int n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,7 @@ def lib():
             "svm_score": [P, P, P, P, I, F, P, P, P],
             "rgbd_ctx_set_tuning": [P, I, I],
             "rgbd_track_nearest": [P, P, I, P, I, P, P],
+            "rgbd_debug_expm1": [P, P, I, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -226,6 +227,14 @@ def rgbd_track_nearest(ctx, prev, cur, match=None, stream=None):
     _check(lib().rgbd_track_nearest(ctx.handle, _p(prev), n_prev, _p(cur) if n_cur else None, n_cur, _p(match),
                                     _stream(stream)))
     return match
+
+
+def rgbd_debug_expm1(z, stream=None):
+    """e^z - 1 as the tensor-core epilogue evaluates it (z: float32 CUDA tensor)."""
+    z = z.contiguous()
+    out = torch.empty_like(z)
+    _check(lib().rgbd_debug_expm1(_p(z), _p(out), z.numel(), _stream(stream)))
+    return out
 
 
 def lbp_normalize_features(ctx, feats, x_dtype, k_pad=None, x_scale=448.0, nbins=NBINS, stream=None):

@@ -103,7 +103,6 @@ struct TcParams {
     uint32_t* status;
     uint32_t idesc_main;
     uint32_t idesc_second;
-    int kind;         // 0 = f16 (bf16), 1 = f8f6f4 (e4m3), 2 = tf32
     int passes;       // 1, or 3 for split bf16 operands (RGBD_DT_BF16X3)
 };
 
@@ -260,43 +259,23 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;             // 128-byte swizzle
     return d;
 }
-template <int CG>
-__device__ __forceinline__ void mma_issue(int kind, uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    if (CG == 1) {
-        if (kind == 0) {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(a), "l"(b), "r"(idesc), "r"(acc));
-        } else if (kind == 1) {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(a), "l"(b), "r"(idesc), "r"(acc));
-        } else {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(a), "l"(b), "r"(idesc), "r"(acc));
-        }
+// KIND: 0 = kind::f16 (bf16 operands), 1 = kind::f8f6f4 (E4M3), 2 = kind::tf32.
+template <int CG, int KIND>
+__device__ __forceinline__ void mma_issue(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+#define RGBD_MMA_SS(CGS, KS)                                                                          \
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"                                   \
+                 "tcgen05.mma.cta_group::" CGS ".kind::" KS " [%0], %1, %2, %3, p;\n\t}" ::"r"(d), "l"(a), \
+                 "l"(b), "r"(idesc), "r"(acc))
+    if constexpr (CG == 1) {
+        if constexpr (KIND == 0) RGBD_MMA_SS("1", "f16");
+        else if constexpr (KIND == 1) RGBD_MMA_SS("1", "f8f6f4");
+        else RGBD_MMA_SS("1", "tf32");
     } else {
-        if (kind == 0) {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(a), "l"(b), "r"(idesc), "r"(acc));
-        } else if (kind == 1) {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(a), "l"(b), "r"(idesc), "r"(acc));
-        } else {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(a), "l"(b), "r"(idesc), "r"(acc));
-        }
+        if constexpr (KIND == 0) RGBD_MMA_SS("2", "f16");
+        else if constexpr (KIND == 1) RGBD_MMA_SS("2", "f8f6f4");
+        else RGBD_MMA_SS("2", "tf32");
     }
+#undef RGBD_MMA_SS
 }
 // D (+)= A B^T with A (bf16, 128 rows per CTA) in tensor memory and B in shared memory.
 template <int CG>
@@ -340,6 +319,19 @@ __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sy
           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),           \
           "=r"(v[15])                                                                                        \
         : "r"(taddr))
+// e^z - 1.  The near-flat RBF gives |z| = gamma |d^2 - r| of order 1e-3, where the Taylor series
+// z + z^2/2! + ... + z^6/6! (Horner form) is exact to fp32 rounding: for |z| < 2^-5 the first
+// omitted term is below 2^-30 |z| / 5040.  Larger arguments use expm1f.
+__device__ __forceinline__ float expm1_near0(float z) {
+    if (fabsf(z) < 0.03125f) {
+        float q = fmaf(z, 1.0f / 720.0f, 1.0f / 120.0f);
+        q = fmaf(z, q, 1.0f / 24.0f);
+        q = fmaf(z, q, 1.0f / 6.0f);
+        q = fmaf(z, q, 0.5f);
+        return fmaf(z * z, q, z);
+    }
+    return expm1f(z);
+}
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 
@@ -355,7 +347,7 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 // reads the operands of both CTAs and writes G and D into both CTAs' tensor memory (each CTA
 // holds its own rows).  All copies count on CTA 0's barriers, and CTA 0's commits arrive on
 // both CTAs' barriers.  Per MMA each CTA supplies 8 KB of operands instead of 12 KB.
-template <int MODE>
+template <int MODE, int KIND>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     rbf_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_sv,
                   const __grid_constant__ CUtensorMap tm_coef, const __grid_constant__ CUtensorMap tm_x2,
@@ -581,12 +573,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         break;
                     }
                     const uint32_t sa = base + (uint32_t)stage * L::STAGE;
+                    const uint64_t a0 = sdesc(sa), b0 = sdesc(sa + X_TILE);
+                    // K step ks starts 32 bytes further along the swizzled rows: +2 in the
+                    // descriptor's address field (16-byte units)
+                    mma_issue<CG, KIND>(tmem, a0, b0, p.idesc_main, kt > 0 ? 1u : 0u);
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t a = sdesc(sa + ks * 32);
-                        const uint64_t bd = sdesc(sa + X_TILE + ks * 32);
-                        mma_issue<CG>(p.kind, tmem, a, bd, p.idesc_main, (kt > 0 || ks > 0) ? 1u : 0u);
-                    }
+                    for (int ks = 1; ks < 4; ++ks)
+                        mma_issue<CG, KIND>(tmem, a0 + 2u * ks, b0 + 2u * ks, p.idesc_main, 1u);
                     if (PAIR)
                         tc_commit2_mc(bar(B_EMPTY + stage), (uint16_t)0x3);
                     else if (MC)
@@ -699,8 +692,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         const int col = n0 + c * 64 + half * 32 + j;
                         const float d0 = xs + __ldg(p.svsq + col) - 2.f * p.gscale * __uint_as_float(v[j]);
                         const float d1 = xs + __ldg(p.svsq + col + 1) - 2.f * p.gscale * __uint_as_float(v[j + 1]);
-                        const __nv_bfloat162 hv = __floats2bfloat162_rn(expm1f(-p.gamma * (d0 - r)),
-                                                                        expm1f(-p.gamma * (d1 - r)));
+                        const __nv_bfloat162 hv = __floats2bfloat162_rn(expm1_near0(-p.gamma * (d0 - r)),
+                                                                        expm1_near0(-p.gamma * (d1 - r)));
                         pk[half * 16 + (j >> 1)] = *reinterpret_cast<const uint32_t*>(&hv);
                     }
                 }
@@ -884,6 +877,35 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
     return RGBD_OK;
 }
 
+// Launches one instantiation: single CTAs on a (row blocks, splits) grid, pairs as clusters of
+// two along the rows (the row-block count rounded up to even).
+template <int MODE, int KIND>
+cudaError_t launch_mode(const TcPlan& pl, const TcParams& p, const rgbd_svm* m, const CUtensorMap& tm_x,
+                        const CUtensorMap& tm_x2, cudaStream_t s) {
+    constexpr int smem = Lay<MODE>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(rbf_tc_kernel<MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (MODE == MODE_SINGLE) {
+        dim3 grid(pl.mt, pl.splits);
+        rbf_tc_kernel<MODE, KIND><<<grid, NUM_THREADS, smem, s>>>(tm_x, m->tm_sv, m->tm_coef, tm_x2, m->tm_sv_lo, p);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((pl.mt + 1) / 2 * 2), (unsigned)pl.splits, 1);
+    cfg.blockDim = dim3(NUM_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, rbf_tc_kernel<MODE, KIND>, tm_x, m->tm_sv_half,
+                              MODE == MODE_PAIR ? m->tm_coef_half : m->tm_coef, tm_x2, m->tm_sv_lo_half, p);
+}
+
 int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n, float x_scale,
               float* scores, int32_t* labels, cudaStream_t s, const TcPlan& pl, char* ws) {
     float* part = (float*)ws;
@@ -923,46 +945,27 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     const int mma_m = mode == MODE_PAIR ? 2 * BM : BM;  // a pair's MMA covers both CTAs' rows
     p.idesc_main = make_idesc(pl.fmt, pl.fmt, mma_m, BN);
     p.idesc_second = make_idesc(1, 1, mma_m, m->C_pad);
-    p.kind = pl.kind;
     p.passes = pl.passes;
     cudaError_t e;
-    if (mode == MODE_SINGLE) {
-        e = cudaFuncSetAttribute(rbf_tc_kernel<MODE_SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 Lay<MODE_SINGLE>::SMEM);
-        if (e != cudaSuccess) return cuda_error(e, "svm_score: tc smem attribute");
-        dim3 grid(pl.mt, pl.splits);
-        rbf_tc_kernel<MODE_SINGLE><<<grid, NUM_THREADS, Lay<MODE_SINGLE>::SMEM, s>>>(tm_x, m->tm_sv, m->tm_coef,
-                                                                                     tm_x2, m->tm_sv_lo, p);
-        e = cudaGetLastError();
-    } else {
-        const int smem = mode == MODE_MC ? Lay<MODE_MC>::SMEM : Lay<MODE_PAIR>::SMEM;
-        e = mode == MODE_MC ? cudaFuncSetAttribute(rbf_tc_kernel<MODE_MC>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-                            : cudaFuncSetAttribute(rbf_tc_kernel<MODE_PAIR>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return cuda_error(e, "svm_score: tc smem attribute");
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)((pl.mt + 1) / 2 * 2), (unsigned)pl.splits, 1);
-        cfg.blockDim = dim3(NUM_THREADS, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        if (mode == MODE_MC)
-            e = cudaLaunchKernelEx(&cfg, rbf_tc_kernel<MODE_MC>, tm_x, m->tm_sv_half, m->tm_coef, tm_x2,
-                                   m->tm_sv_lo_half, p);
-        else
-            e = cudaLaunchKernelEx(&cfg, rbf_tc_kernel<MODE_PAIR>, tm_x, m->tm_sv_half, m->tm_coef_half, tm_x2,
-                                   m->tm_sv_lo_half, p);
+    switch (mode * 3 + pl.kind) {
+        case MODE_SINGLE * 3 + 0: e = launch_mode<MODE_SINGLE, 0>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_SINGLE * 3 + 1: e = launch_mode<MODE_SINGLE, 1>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_SINGLE * 3 + 2: e = launch_mode<MODE_SINGLE, 2>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_MC * 3 + 0: e = launch_mode<MODE_MC, 0>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_MC * 3 + 1: e = launch_mode<MODE_MC, 1>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_MC * 3 + 2: e = launch_mode<MODE_MC, 2>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_PAIR * 3 + 0: e = launch_mode<MODE_PAIR, 0>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_PAIR * 3 + 1: e = launch_mode<MODE_PAIR, 1>(pl, p, m, tm_x, tm_x2, s); break;
+        default: e = launch_mode<MODE_PAIR, 2>(pl, p, m, tm_x, tm_x2, s); break;
     }
     if (e != cudaSuccess) return cuda_error(e, "svm_score: tc launch");
     return launch_reduce_scores(part, ref, pl.splits, n, m->C, m->C_pad, m->asum, m->asum_tile, pl.tps, pl.nt,
                                 m->bias, m->gamma, scores, labels, s);
+}
+
+__global__ void expm1_probe_kernel(const float* __restrict__ z, float* __restrict__ out, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = expm1_near0(z[i]);
 }
 
 }  // namespace
@@ -991,3 +994,12 @@ int score_rbf_tc_external_ws(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, co
 }
 
 }  // namespace rgbd
+
+extern "C" int rgbd_debug_expm1(const float* z, float* out, int n, void* stream) {
+    using namespace rgbd;
+    if (n < 0 || (n > 0 && (!z || !out))) return set_error(RGBD_ERR_ARG, "rgbd_debug_expm1: n %d, z %p, out %p", n, z, out);
+    if (n == 0) return RGBD_OK;
+    expm1_probe_kernel<<<std::min((n + 255) / 256, 1024), 256, 0, (cudaStream_t)stream>>>(z, out, n);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RGBD_OK : cuda_error(e, "rgbd_debug_expm1");
+}

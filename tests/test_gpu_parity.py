@@ -228,6 +228,25 @@ def test_rbf_tensor_core_paths(B, ctx, orc, dt, n, n_sv, C):
     assert err <= bound, err
 
 
+def test_epilogue_expm1_accuracy(B):
+    """The epilogue's e^z - 1 (Taylor polynomial near 0, expm1f beyond 2^-5) against fp64 and
+    against CUDA's expm1f (torch.expm1): within 2 ulp of the exact value (3 of expm1f) everywhere, across the
+    switch point and at the extremes of the scoring arguments."""
+    rng = np.random.default_rng(5)
+    z = np.concatenate([rng.uniform(-0.04, 0.04, 200000), rng.uniform(-1e-3, 1e-3, 100000),
+                        rng.normal(0, 1e-6, 10000), np.linspace(-0.0313, -0.0312, 1001),
+                        np.linspace(0.0312, 0.0313, 1001), rng.uniform(-20, 5, 10000),
+                        [0.0, -0.0, 0.03125, -0.03125, 1e-30, -1e-30]]).astype(np.float32)
+    zt = torch.from_numpy(z).cuda()
+    ours = B.rgbd_debug_expm1(zt).cpu().numpy().astype(np.float64)
+    cuda = torch.expm1(zt).cpu().numpy().astype(np.float64)
+    exact = np.expm1(z.astype(np.float64))
+    ulp = np.spacing(np.abs(exact).astype(np.float32)).astype(np.float64)
+    ulp = np.maximum(ulp, np.float64(np.finfo(np.float32).tiny))
+    assert np.max(np.abs(ours - exact) / ulp) <= 2.0
+    assert np.max(np.abs(ours - cuda) / ulp) <= 3.0
+
+
 @pytest.mark.parametrize("mc", [3, 1, 2])
 @pytest.mark.parametrize("dt", ["bf16", "fp8", "tf32", "bf16x3"])
 def test_tensor_core_pairing_modes(B, ctx, orc, dt, mc):
