@@ -39,6 +39,28 @@ DT_CODE = {"f32": 1, "bf16": 2, "fp8": 3, "tf32": 4, "bf16x3": 5}
 X_ELEM = {"f32": 4, "tf32": 4, "bf16": 2, "fp8": 1, "bf16x3": 4}
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the batch workload (the
+# profiles/ summaries give the commands), valid only for the kernel source and launch layout
+# they were taken with: (source file, sha256 prefix, layout key) -> bytes.  A changed kernel or
+# layout reports null.
+MEASURED_TRAFFIC = {
+    "k1": ("lbp.cu", "05c8af8a79629ba6", "ctas2/bf16", 173_327_360 + 199_240_960),
+    "k2": ("svm_tc.cu", "18b937fa0e913c49", "splits4/pair/bf16", 616_600_832 + 3_036_416),
+}
+
+
+def measured_traffic(stage, layout):
+    import hashlib
+    fname, digest, key, nbytes = MEASURED_TRAFFIC[stage]
+    path = os.path.join(ROOT, "paper_1504_01883_gb300", "csrc", fname)
+    try:
+        with open(path, "rb") as f:
+            ok = hashlib.sha256(f.read()).hexdigest()[:16] == digest
+    except OSError:
+        ok = False
+    return nbytes if ok and layout == key else None
+
+
 def peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -356,10 +378,13 @@ def main():
         peak_t = pk["bf16_tflops"] * NOMINAL_RATIO[dt]
     rl_k1 = {"kernel": "lbp_fused_kernel<128>", "bound": "hbm", "achieved": round(k1_gbs, 1),
              "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(k1_gbs / pk["hbm_gbs"], 4),
-             "traffic": None, "algorithmic_bytes": k1_bytes, "ms": round(k1_ms, 4), "peak_source": src}
+             "traffic": measured_traffic("k1", f"ctas{tuning.lbp_ctas_per_sm}/{dt}"),
+             "algorithmic_bytes": k1_bytes, "ms": round(k1_ms, 4), "peak_source": src}
     rl_k2 = {"kernel": "rbf_tc_kernel" if dt != "f32" else "rbf_tiled_kernel", "bound": "tensor" if peak_t else "alu",
              "achieved": round(k2_tflops, 1), "peak": round(peak_t, 1) if peak_t else None, "unit": "TFLOP/s",
-             "frac": round(k2_tflops / peak_t, 4) if peak_t else None, "traffic": None,
+             "frac": round(k2_tflops / peak_t, 4) if peak_t else None,
+             "traffic": measured_traffic("k2", f"splits{tuning.tc_splits}/"
+                                               f"{autotune.PAIRING_NAMES.get(tuning.tc_multicast, 'auto')}/{dt}"),
              "algorithmic_flops": k2_flops, "ms": round(k2_ms, 4), "peak_source": src}
     dominant = rl_k2 if k2_ms >= k1_ms else rl_k1
     roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
