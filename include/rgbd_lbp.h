@@ -265,6 +265,32 @@ int svm_score(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* 
 int rgbd_track_nearest(rgbd_ctx* ctx, const rgbd_rect* prev, int n_prev, const rgbd_rect* cur, int n_cur,
                        int32_t* match, void* stream);
 
+/* Per-stream identities across a batch of frames (Section 2.3: each face is followed to the
+ * nearest rectangle centre in the next frame of its camera, and the stream's data set is
+ * updated at every frame).  The state of every stream -- the rects of its last served frame
+ * and the identity of each of those faces -- stays on the device between calls.
+ * For each frame f of the batch, in order:
+ *   1. every previous face j of stream frame_stream[f] picks the current face of f whose
+ *      centre is nearest (exact, as (2x + w, 2y + h); lowest index on ties);
+ *   2. a current face picked by one or more previous faces takes the identity of the nearest
+ *      of them (lowest j on ties); a face picked by none takes its own label;
+ *   3. the stream's state becomes f's first min(faces, max_faces) faces and their identities.
+ *   state_rects  rgbd_rect [n_streams][max_faces] (device, caller-owned, updated)
+ *   state_ids    int32 [n_streams][max_faces]     (device, updated)
+ *   state_count  int32 [n_streams]                (device, updated; zero = no previous frame)
+ *   frame_stream int32 [n_frames] stream id of each frame (device)
+ *   frame_start  int32 [n_frames + 1]: faces of frame f are rects/labels/ids
+ *                [frame_start[f], frame_start[f + 1]) (device)
+ *   rects        rgbd_rect [n] (device; the frame field is ignored)
+ *   labels       int32 [n] classifier labels (device), ids int32 [n] identities (device, out)
+ * max_faces is 1..256.  A frame whose stream id is out of range keeps its labels and leaves the
+ * states alone; a frame whose face range is out of bounds is skipped; both set
+ * RGBD_STATUS_BAD_RECT.  Asynchronous on stream.  Errors: RGBD_ERR_ARG. */
+int rgbd_track_streams(rgbd_ctx* ctx, rgbd_rect* state_rects, int32_t* state_ids, int32_t* state_count,
+                       int n_streams, int max_faces, int n_frames, const int32_t* frame_stream,
+                       const int32_t* frame_start, const rgbd_rect* rects, int n, const int32_t* labels,
+                       int32_t* ids, void* stream);
+
 /* Size of the fixed scratch array behind svm_score_noalloc (16 MiB per GPU). */
 #define RGBD_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -21,7 +21,7 @@ __all__ = [
     "build", "lib", "rect_coord_q16", "crop", "median_nonzero", "valid_mask", "lbp_code",
     "lbp_codes", "uniform_table", "histograms", "features_batch", "normalize_f64",
     "normalize_f32", "f32_to_bf16", "f32_to_e4m3", "e4m3_to_f64", "svm_rbf", "svm_linear",
-    "argmax", "track_nearest", "RECT_DTYPE", "LBP_GE", "LBP_NBR_IGNORE_MASK",
+    "argmax", "track_nearest", "track_streams", "RECT_DTYPE", "LBP_GE", "LBP_NBR_IGNORE_MASK",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -270,6 +270,24 @@ def argmax(scores):
 
 
 # ---- Section 2.3: nearest-centre tracking ---------------------------------------------------
+
+def track_streams(state, frame_stream, frame_start, rects, labels):
+    """Per-stream tracking over a batch (Section 2.3); `state` = dict(rects [S][M] RECT_DTYPE,
+    ids int32 [S][M], count int32 [S]) is updated in place.  Returns int32 ids [n]."""
+    rects = np.ascontiguousarray(rects, RECT_DTYPE)
+    labels = np.ascontiguousarray(labels, np.int32)
+    fs = np.ascontiguousarray(frame_stream, np.int32)
+    st = np.ascontiguousarray(frame_start, np.int32)
+    S, M = state["ids"].shape
+    for k in ("rects", "ids", "count"):
+        assert state[k].flags["C_CONTIGUOUS"]
+    L = lib()
+    L.orc_track_streams.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] * 3 + [ctypes.c_void_p] * 5
+    ids = np.zeros(len(rects), np.int32)
+    L.orc_track_streams(_p(state["rects"]), _p(state["ids"]), _p(state["count"]), S, M, len(fs), _p(fs), _p(st),
+                        _p(rects), _p(labels), _p(ids))
+    return ids
+
 
 def track_nearest(prev, cur):
     """For each previous rect, the index of the nearest current rect of the same stream, or -1."""

@@ -406,3 +406,67 @@ void orc_track_nearest(const orc_rect* prev, int n_prev, const orc_rect* cur, in
         match[i] = best;
     }
 }
+
+/* Per-stream tracking over a batch of frames (Section 2.3: each face of the previous frame of
+ * a stream is followed to the nearest face centre of the next frame, and the stream's data set
+ * is updated at every frame).  For each frame f in batch order, with s = frame_stream[f]:
+ *   1. every previous face j of s (state) is matched to its nearest current face of f
+ *      (orc_track_nearest's rule: Euclidean distance of centres, lowest index on ties);
+ *   2. a current face matched by some previous faces takes the identity of the nearest of
+ *      them (lowest j on ties); every other current face takes its own classifier label;
+ *   3. the state of s becomes f's first min(faces, max_faces) faces and their identities.
+ * state_rects [n_streams][max_faces], state_ids [n_streams][max_faces], state_count
+ * [n_streams] are updated in place; ids [n] receives each face's identity.  A frame whose
+ * stream id is out of range leaves every state untouched and its faces keep their labels. */
+void orc_track_streams(orc_rect* state_rects, int32_t* state_ids, int32_t* state_count, int n_streams,
+                       int max_faces, int n_frames, const int32_t* frame_stream, const int32_t* frame_start,
+                       const orc_rect* rects, const int32_t* labels, int32_t* ids) {
+    for (int f = 0; f < n_frames; ++f) {
+        const int s = frame_stream[f];
+        const int k0 = frame_start[f], nf = frame_start[f + 1] - frame_start[f];
+        for (int k = 0; k < nf; ++k) ids[k0 + k] = labels[k0 + k];
+        if (s < 0 || s >= n_streams) continue;
+        orc_rect* prev = state_rects + (size_t)s * max_faces;
+        int32_t* prev_id = state_ids + (size_t)s * max_faces;
+        const int np = state_count[s];
+        /* step 1 on copies whose stream field is the same, so orc_track_nearest compares them */
+        orc_rect* p = (orc_rect*)malloc(sizeof(orc_rect) * (size_t)(np > 0 ? np : 1));
+        orc_rect* c = (orc_rect*)malloc(sizeof(orc_rect) * (size_t)(nf > 0 ? nf : 1));
+        int32_t* m = (int32_t*)malloc(sizeof(int32_t) * (size_t)(np > 0 ? np : 1));
+        for (int j = 0; j < np; ++j) {
+            p[j] = prev[j];
+            p[j].frame = 0;
+        }
+        for (int k = 0; k < nf; ++k) {
+            c[k] = rects[k0 + k];
+            c[k].frame = 0;
+        }
+        orc_track_nearest(p, np, c, nf, m);
+        /* step 2: the nearest of the previous faces that chose current face k */
+        for (int k = 0; k < nf; ++k) {
+            int best = -1;
+            double bd = 0.0;
+            const double cx = c[k].x + c[k].w / 2.0, cy = c[k].y + c[k].h / 2.0;
+            for (int j = 0; j < np; ++j) {
+                if (m[j] != k) continue;
+                const double px = p[j].x + p[j].w / 2.0, py = p[j].y + p[j].h / 2.0;
+                const double d = sqrt((cx - px) * (cx - px) + (cy - py) * (cy - py));
+                if (best < 0 || d < bd) {
+                    best = j;
+                    bd = d;
+                }
+            }
+            if (best >= 0) ids[k0 + k] = prev_id[best];
+        }
+        /* step 3 */
+        const int keep = nf < max_faces ? nf : max_faces;
+        for (int k = 0; k < keep; ++k) {
+            prev[k] = rects[k0 + k];
+            prev_id[k] = ids[k0 + k];
+        }
+        state_count[s] = keep;
+        free(p);
+        free(c);
+        free(m);
+    }
+}

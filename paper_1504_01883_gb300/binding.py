@@ -79,6 +79,7 @@ def lib():
             "rgbd_ctx_set_tuning": [P, I, I],
             "rgbd_track_nearest": [P, P, I, P, I, P, P],
             "rgbd_debug_expm1": [P, P, I, P],
+            "rgbd_track_streams": [P, P, P, P, I, I, I, P, P, P, I, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -227,6 +228,32 @@ def rgbd_track_nearest(ctx, prev, cur, match=None, stream=None):
     _check(lib().rgbd_track_nearest(ctx.handle, _p(prev), n_prev, _p(cur) if n_cur else None, n_cur, _p(match),
                                     _stream(stream)))
     return match
+
+
+class TrackState:
+    """Device-resident per-stream tracking state: the rects of each stream's last served frame
+    and the identities of those faces (see rgbd_track_streams)."""
+
+    def __init__(self, n_streams, max_faces=64, device=None):
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.n_streams, self.max_faces = n_streams, max_faces
+        self.rects = torch.zeros((n_streams, max_faces, 5), dtype=torch.int32, device=dev)
+        self.ids = torch.full((n_streams, max_faces), -1, dtype=torch.int32, device=dev)
+        self.count = torch.zeros((n_streams,), dtype=torch.int32, device=dev)
+
+
+def rgbd_track_streams(ctx, state, frame_stream, frame_start, rects, labels, ids=None, stream=None):
+    """Identities of a batch's faces from each stream's previous frame (Section 2.3); updates
+    `state` (a TrackState).  frame_stream int32 [F], frame_start int32 [F + 1], rects int32 [n][5],
+    labels int32 [n] (all CUDA).  Returns ids int32 [n]."""
+    n = rects.shape[0]
+    if ids is None:
+        ids = torch.empty((n,), dtype=torch.int32, device=rects.device)
+    _check(lib().rgbd_track_streams(ctx.handle, _p(state.rects), _p(state.ids), _p(state.count), state.n_streams,
+                                    state.max_faces, frame_stream.shape[0], _p(frame_stream), _p(frame_start),
+                                    _p(rects) if n else None, n, _p(labels) if n else None, _p(ids) if n else None,
+                                    _stream(stream)))
+    return ids
 
 
 def rgbd_debug_expm1(z, stream=None):

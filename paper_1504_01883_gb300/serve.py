@@ -61,6 +61,7 @@ class FrameRequest:
     t_done: float = 0.0
     scores: np.ndarray | None = None
     labels: np.ndarray | None = None
+    ids: np.ndarray | None = None         # tracked identities (Section 2.3), batched path only
 
 
 class MemoryAdmission:
@@ -93,6 +94,7 @@ class _Batch:
     labels_h: torch.Tensor
     n: int
     buffer: int
+    ids_h: torch.Tensor | None = None
 
 
 @dataclass
@@ -146,13 +148,19 @@ class BatchServer:
                 "labels": torch.empty((max_faces,), dtype=torch.int32, device=self.dev),
                 "scores_h": torch.empty((max_faces, C), dtype=torch.float32).pin_memory(),
                 "labels_h": torch.empty((max_faces,), dtype=torch.int32).pin_memory(),
+                # frame -> stream ids and face ranges of the batch, for the tracking step
+                "meta_h": torch.empty((2 * n_slots + 1,), dtype=torch.int32).pin_memory(),
+                "meta": torch.empty((2 * n_slots + 1,), dtype=torch.int32, device=self.dev),
+                "ids": torch.empty((max_faces,), dtype=torch.int32, device=self.dev),
+                "ids_h": torch.empty((max_faces,), dtype=torch.int32).pin_memory(),
             })
         self.compute = torch.cuda.Stream(device=self.dev)
         self.copy = torch.cuda.Stream(device=self.dev)
         self.admission = admission or MemoryAdmission(n_slots)
         self.slot_ready = {}   # slot -> event recorded after its upload
-        # per-stream state kept on the device: the labels of the last served frame
-        self.last_labels = torch.full((len(streams), 12), -1, dtype=torch.int32, device=self.dev)
+        # per-stream state kept on the device: the faces of each stream's last served frame and
+        # their identities (Section 2.3 tracking), updated by every batch in arrival order
+        self.track = B.TrackState(len(streams), max_faces=16, device=self.dev)
 
     def _frame(self, req):
         s = self.streams[req.stream]
@@ -178,6 +186,10 @@ class BatchServer:
                 rows.append((req.slot, int(r["x"]), int(r["y"]), int(r["w"]), int(r["h"])))
         n = len(rows)
         buf["rects_h"][:n] = torch.tensor(rows, dtype=torch.int32)
+        nfr = len(frames)
+        starts = np.cumsum([0] + [req.n_faces for req in frames])
+        buf["meta_h"][:nfr] = torch.tensor([req.stream for req in frames], dtype=torch.int32)
+        buf["meta_h"][nfr:2 * nfr + 1] = torch.from_numpy(starts.astype(np.int32))
         cs = self.compute
         for req in frames:
             cs.wait_event(self.slot_ready.pop(req.slot))
@@ -189,11 +201,15 @@ class BatchServer:
                                  out={"x": buf["x"][:n], "xsq": buf["xsq"][:n]}, stream=cs)
             B.svm_score(self.ctx, self.model, buf["x"][:n], buf["xsq"][:n], scores=buf["scores"][:n],
                         labels=buf["labels"][:n], stream=cs)
+            buf["meta"][:2 * nfr + 1].copy_(buf["meta_h"][:2 * nfr + 1], non_blocking=True)
+            B.rgbd_track_streams(self.ctx, self.track, buf["meta"][:nfr], buf["meta"][nfr:2 * nfr + 1], rects,
+                                 buf["labels"][:n], ids=buf["ids"][:n], stream=cs)
             buf["scores_h"][:n].copy_(buf["scores"][:n], non_blocking=True)
             buf["labels_h"][:n].copy_(buf["labels"][:n], non_blocking=True)
+            buf["ids_h"][:n].copy_(buf["ids"][:n], non_blocking=True)
             done = torch.cuda.Event()
             done.record(cs)
-        return _Batch(frames, done, buf["scores_h"], buf["labels_h"], n, buf_id)
+        return _Batch(frames, done, buf["scores_h"], buf["labels_h"], n, buf_id, buf["ids_h"])
 
     def _complete(self, batch, t0, report, keep_results):
         now = time.perf_counter() - t0
@@ -203,6 +219,8 @@ class BatchServer:
             if keep_results:
                 req.scores = batch.scores_h[off:off + k].numpy().copy()
                 req.labels = batch.labels_h[off:off + k].numpy().copy()
+                if batch.ids_h is not None:
+                    req.ids = batch.ids_h[off:off + k].numpy().copy()
             off += k
             req.t_done = now
             report.latencies_ms.append(1000.0 * (now - req.t_arrival))

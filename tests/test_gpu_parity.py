@@ -321,3 +321,41 @@ def test_track_nearest(B, ctx, orc):
         arr["h"] = arr["w"]
     m = B.rgbd_track_nearest(ctx, B.rects_tensor(prev), B.rects_tensor(cur))
     assert (m.cpu().numpy() == orc.track_nearest(prev, cur)).all()
+
+
+def test_track_streams_against_oracle(B, ctx, orc):
+    """Per-stream identities over a sequence of batches: ids and the device-resident state equal
+    the oracle's, including streams that skip batches, empty frames, repeated streams within a
+    batch, more faces than the state holds and an out-of-range stream id."""
+    R = orc.RECT_DTYPE
+    rng = np.random.default_rng(23)
+    S, M = 6, 5
+    state = B.TrackState(S, M)
+    ref = {"rects": np.zeros((S, M), R), "ids": np.full((S, M), -1, np.int32), "count": np.zeros(S, np.int32)}
+    for it in range(25):
+        nfr = int(rng.integers(1, 9))
+        fs = rng.integers(0, S, nfr).astype(np.int32)
+        if it == 7:
+            fs[0] = S + 3  # out of range: labels pass through
+        counts = rng.integers(0, 9, nfr)
+        start = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+        n = int(start[-1])
+        rects = np.zeros(n, R)
+        rects["frame"] = 99
+        rects["x"] = rng.integers(-20, 620, n)
+        rects["y"] = rng.integers(-20, 460, n)
+        rects["w"] = rng.integers(8, 120, n)
+        rects["h"] = rng.integers(8, 120, n)
+        labels = rng.integers(0, 30, n).astype(np.int32)
+        want = orc.track_streams(ref, fs, start, rects, labels)
+        got = B.rgbd_track_streams(ctx, state, torch.from_numpy(fs).cuda(), torch.from_numpy(start).cuda(),
+                                   B.rects_tensor(rects), torch.from_numpy(labels).cuda())
+        assert (got.cpu().numpy() == want).all(), it
+        ctx.status(clear=True)
+    assert (state.count.cpu().numpy() == ref["count"]).all()
+    for s in range(S):
+        c = int(ref["count"][s])
+        assert (state.ids.cpu().numpy()[s, :c] == ref["ids"][s, :c]).all()
+        got_r = state.rects.cpu().numpy()[s, :c]
+        for k, f in enumerate(["frame", "x", "y", "w", "h"]):
+            assert (got_r[:, k] == ref["rects"][f][s, :c]).all()

@@ -374,3 +374,85 @@ def test_track_nearest_hand_cases(orc):
             d = np.hypot((c["x"][same] + c["w"][same] / 2) - (p["x"][i] + p["w"][i] / 2),
                          (c["y"][same] + c["h"][same] / 2) - (p["y"][i] + p["h"][i] / 2))
             assert got[i] == same[np.argmin(d)]
+
+
+def _track_state(orc, S, M):
+    return {"rects": np.zeros((S, M), orc.RECT_DTYPE), "ids": np.full((S, M), -1, np.int32),
+            "count": np.zeros(S, np.int32)}
+
+
+def test_track_streams_hand_cases(orc):
+    """Section 2.3: identities follow the nearest centre from frame to frame, per stream."""
+    R = orc.RECT_DTYPE
+    st = _track_state(orc, 3, 4)
+    # batch 1: stream 0 sees A (centre 50,50) and B (centre 200,100); stream 2 sees C
+    ids = orc.track_streams(st, [0, 2], [0, 2, 3],
+                            np.array([(0, 40, 40, 20, 20), (0, 190, 90, 20, 20), (0, 300, 300, 40, 40)], R),
+                            [7, 3, 5])
+    assert list(ids) == [7, 3, 5]                      # empty state: the classifier's labels
+    assert list(st["count"]) == [2, 0, 1]
+    # batch 2: stream 0's faces moved a little and come in the other order, plus a new face D;
+    # the classifier now calls B "1" (a misclassification tracking corrects); stream 1 starts
+    ids = orc.track_streams(st, [0, 1], [0, 3, 4],
+                            np.array([(0, 195, 95, 20, 20), (0, 45, 42, 20, 20), (0, 500, 10, 30, 30),
+                                      (0, 10, 10, 10, 10)], R),
+                            [1, 1, 9, 4])
+    assert list(ids) == [3, 7, 9, 4]
+    assert list(st["count"]) == [3, 1, 1] and list(st["ids"][0][:3]) == [3, 7, 9]
+    # batch 3: two frames of stream 0.  First only A remains (B and D also pick it as their
+    # nearest current face, but A's previous face is the nearest of the three); then A and a
+    # face where B was
+    ids = orc.track_streams(st, [0, 0], [0, 1, 3],
+                            np.array([(0, 47, 44, 20, 20), (0, 48, 44, 20, 20), (0, 196, 96, 20, 20)], R),
+                            [2, 2, 8])
+    assert list(ids) == [7, 7, 8]
+    assert list(st["count"]) == [2, 1, 1] and list(st["ids"][0][:2]) == [7, 8]
+    # stream id out of range: labels pass through, no state changes
+    before = {k: v.copy() for k, v in st.items()}
+    ids = orc.track_streams(st, [5], [0, 1], np.array([(0, 0, 0, 9, 9)], R), [6])
+    assert list(ids) == [6] and all((st[k] == before[k]).all() for k in st)
+    # more faces than the state holds: all get identities, the first max_faces are kept
+    st2 = _track_state(orc, 1, 2)
+    ids = orc.track_streams(st2, [0], [0, 3], np.array([(0, i * 50, 0, 10, 10) for i in range(3)], R), [1, 2, 3])
+    assert list(ids) == [1, 2, 3] and st2["count"][0] == 2
+
+
+def test_track_streams_brute_force(orc):
+    """Random batches against a direct numpy restatement of the three steps."""
+    R = orc.RECT_DTYPE
+    rng = np.random.default_rng(11)
+    S, M = 4, 5
+    st = _track_state(orc, S, M)
+    ref = {s: ([], []) for s in range(S)}  # stream -> (rect rows, ids)
+    for _ in range(12):
+        nfr = int(rng.integers(1, 6))
+        fs = rng.integers(0, S, nfr)
+        counts = rng.integers(0, 8, nfr)
+        start = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+        n = int(start[-1])
+        rects = np.zeros(n, R)
+        rects["x"] = rng.integers(0, 600, n)
+        rects["y"] = rng.integers(0, 440, n)
+        rects["w"] = rng.integers(10, 100, n)
+        rects["h"] = rects["w"]
+        labels = rng.integers(0, 20, n).astype(np.int32)
+        got = orc.track_streams(st, fs, start, rects, labels)
+        want = labels.copy()
+        for f in range(nfr):
+            s, k0, k1 = int(fs[f]), int(start[f]), int(start[f + 1])
+            prev, pid = ref[s]
+            cx = rects["x"][k0:k1] + rects["w"][k0:k1] / 2
+            cy = rects["y"][k0:k1] + rects["h"][k0:k1] / 2
+            chosen = {}
+            for j, (px, py) in enumerate(prev):
+                if k1 == k0:
+                    break
+                d = np.hypot(cx - px, cy - py)
+                k = int(np.argmin(d))  # first minimum = lowest index
+                if k not in chosen or d[k] < chosen[k][0]:
+                    chosen[k] = (d[k], j)
+            for k, (_, j) in chosen.items():
+                want[k0 + k] = pid[j]
+            keep = min(k1 - k0, M)
+            ref[s] = ([(cx[i], cy[i]) for i in range(keep)], [int(want[k0 + i]) for i in range(keep)])
+        assert (got == want).all()

@@ -60,3 +60,38 @@ def test_each_frame_is_the_same_alone_and_in_the_mix():
         clear = (srt[:, -1] - srt[:, -2]) > 5e-5 * scale.max()
         assert (one.labels[clear] == req.labels[clear]).all()
     assert ctx.status() == 0
+
+
+@pytest.mark.gpu
+def test_served_identities_follow_the_tracking_rule():
+    """The batched loop's per-stream device state gives every served face the identity the
+    oracle's Section 2.3 tracking gives when the same frames and labels are replayed in
+    arrival order."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle as orc
+    from paper_1504_01883_gb300 import _build, serve
+    from paper_1504_01883_gb300 import binding as B
+    _build.build()
+    ctx = B.Context(0)
+    dim = 16 * 16 * 59
+    rng = synth.rng_for(98)
+    sv = synth.poisson_counts(rng, 512, dim)
+    a, b = synth.rbf_coefficients(rng, 8, 512)
+    model = B.svm_train_data_pack(ctx, torch.from_numpy(sv.view(np.int16)).cuda(), torch.from_numpy(a).cuda(),
+                                  torch.from_numpy(b).cuda(), gamma=1.0 / dim, dtype="bf16")
+    streams = serve.make_streams(seed=8, n_streams=5, frames_per_stream=3)
+    events = synth.serving_arrivals(seed=8, n_streams=5, seconds=0.4)
+    srv = serve.BatchServer(ctx, model, streams, n_slots=12, max_faces=256)
+    rep, reqs = srv.run(events, keep_results=True, realtime=False)
+    assert rep.frames == len(reqs)
+    state = {"rects": np.zeros((5, 16), orc.RECT_DTYPE), "ids": np.full((5, 16), -1, np.int32),
+             "count": np.zeros(5, np.int32)}
+    order = sorted(range(len(reqs)), key=lambda i: (reqs[i].t_arrival, i))
+    for i in order:
+        req = reqs[i]
+        rects = streams[req.stream].rects[req.index % len(streams[req.stream].rects)]
+        want = orc.track_streams(state, [req.stream], [0, len(rects)], rects, req.labels)
+        assert (req.ids == want).all()
+    assert ctx.status() == 0
