@@ -217,7 +217,8 @@ def run_precision(args):
         labels[dt] = l_out.cpu().numpy()
         sub_scores[dt] = s_out[:oracle_rows].cpu().numpy()
         if dt == "f32":
-            Xs = X[:oracle_rows].cpu().numpy().view(np.uint16)
+            Xbig = X[:int(os.environ.get("PRECISION_FP64_ROWS", "4096"))].cpu().numpy().view(np.uint16)
+            Xs = Xbig[:oracle_rows]
             SVh = SV.cpu().numpy().view(np.uint16)
         model.free()
         del x, q, s_out, l_out
@@ -235,15 +236,35 @@ def run_precision(args):
     srt = np.sort(ref, axis=1)
     margin = srt[:, -1] - srt[:, -2]
     scale = np.abs(a).sum(1)[None, :] + np.abs(b)[None, :]
+    # fp64 labels of a larger row block through the norm expansion and fp64 BLAS (the oracle's
+    # direct sum is too slow for it); checked against the oracle on the rows both cover
+    t1 = time.perf_counter()
+    big = min(n_rows, int(os.environ.get("PRECISION_FP64_ROWS", "4096")))
+    xb = orc.normalize_f64(Xbig)
+    d2 = (xb * xb).sum(1)[:, None] + (sv64 * sv64).sum(1)[None, :] - 2.0 * (xb @ sv64.T)
+    ref_big = np.exp(-gamma * np.maximum(d2, 0.0)) @ a.astype(np.float64).T + b.astype(np.float64)[None, :]
+    del d2
+    t_blas = time.perf_counter() - t1
+    blas_vs_oracle = float(np.abs(ref_big[:oracle_rows] - ref).max())
+    lab_big = orc.argmax(ref_big)
+    sb = np.sort(ref_big, axis=1)
+    margin_big = sb[:, -1] - sb[:, -2]
     for dt in res:
         err = np.abs(sub_scores[dt].astype(np.float64) - ref)
         res[dt]["max_abs_err_vs_fp64"] = float(err.max())
         res[dt]["max_rel_err_vs_fp64"] = float((err / scale).max())
         res[dt]["label_agreement_vs_fp64_sample"] = float((labels[dt][:oracle_rows] == ref_lab).mean())
         res[dt]["label_agreement_vs_f32_all_rows"] = float((labels[dt] == labels["f32"]).mean())
+        agree = labels[dt][:big] == lab_big
+        decided = margin_big > 2.0 * err.max()  # rows whose label that error bound cannot flip
+        res[dt][f"label_agreement_vs_fp64_{big}_rows"] = float(agree.mean())
+        res[dt]["rows_with_fp64_margin_above_2x_error"] = float(decided.mean())
+        res[dt]["label_agreement_where_margin_above_2x_error"] = float(agree[decided].mean())
     return _emit({"workload": f"precision: {n_rows} x {n_sv} SVs x {dim} dims (Poisson(3) counts normalised per "
                               f"cell), {C} classes, gamma=1/dim", "metric": "scoring TFLOP/s, error and label agreement",
                   "results": res, "oracle_rows": oracle_rows, "oracle_s": t_oracle,
+                  "fp64_blas_rows": big, "fp64_blas_s": t_blas, "fp64_blas_vs_oracle_max_abs": blas_vs_oracle,
+                  "fp64_margin_below_1e-6_fraction": float((margin_big < 1e-6).mean()),
                   "fp64_margin_top1_top2": {"min": float(margin.min()), "median": float(np.median(margin))},
                   "peak_source": src})
 

@@ -49,7 +49,8 @@ struct rgbd_svm {
     void* sv = nullptr;       // [n_pad][k_pad] of dtype (float for F32 / TF32)
     float* sv_sq = nullptr;   // [n_pad]
     float* coef = nullptr;    // RBF: float [C][n_pad]; linear: float [C][k_pad]
-    uint16_t* coef_bf16 = nullptr;  // RBF tensor path: bf16 bits [C_pad][n_pad]
+    uint16_t* coef_bf16 = nullptr;  // RBF tensor path: bf16 bits [C_pad][n_pad] ([2][C_pad][n_pad]
+                                    // hi, lo for RGBD_DT_BF16X3)
     float* asum = nullptr;    // [C] sum_i a_ci (accumulated in fp64)
     float* asum_tile = nullptr;  // RBF: [n_pad / kSvTile][C_pad] sum of a_ci over each SV tile (fp64)
     float* bias = nullptr;    // [C]
@@ -59,6 +60,8 @@ struct rgbd_svm {
     CUtensorMap tm_sv_lo_half;
     CUtensorMap tm_coef;
     CUtensorMap tm_coef_half; // half of the classes of a coefficient chunk (2-CTA MMA pairs)
+    CUtensorMap tm_coef_lo;   // RGBD_DT_BF16X3: the same two maps over the lo coefficient plane
+    CUtensorMap tm_coef_lo_half;
     bool has_tmaps = false;
 };
 

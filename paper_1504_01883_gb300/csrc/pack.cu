@@ -4,6 +4,8 @@
 // (tensor-core path), per-class coefficient sums, and the TMA descriptors of the tensor path.
 #include <string.h>
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <new>
 
@@ -12,8 +14,10 @@
 namespace rgbd {
 namespace {
 
+// Coefficients padded to [C][n_pad] fp32 and [C_pad][n_pad] bf16 (round to nearest even); with
+// `split`, a second bf16 plane holds lo = bf16(a - hi).
 __global__ void coef_pad_kernel(const float* __restrict__ coef, int C, int n, int n_pad, int C_pad,
-                                float* __restrict__ out_f32, uint16_t* __restrict__ out_bf16) {
+                                float* __restrict__ out_f32, uint16_t* __restrict__ out_bf16, int split) {
     const size_t total = (size_t)C_pad * n_pad;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -21,10 +25,9 @@ __global__ void coef_pad_kernel(const float* __restrict__ coef, int C, int n, in
         const float v = (c < C && i < n) ? coef[(size_t)c * n + i] : 0.f;
         if (c < C) out_f32[(size_t)c * n_pad + i] = v;
         if (out_bf16) {
-            // round to nearest even
-            uint32_t u = __float_as_uint(v);
-            u += 0x7FFFu + ((u >> 16) & 1u);
-            out_bf16[idx] = (uint16_t)(u >> 16);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            out_bf16[idx] = __bfloat16_as_ushort(hi);
+            if (split) out_bf16[total + idx] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(hi)));
         }
     }
 }
@@ -224,9 +227,12 @@ int svm_train_data_pack(rgbd_ctx* ctx, const uint16_t* sv_feats, int n_sv, int d
         }
         if (coef) {
             TRY_CUDA(cudaMalloc(&m->coef, sizeof(float) * (size_t)m->C * m->n_pad), "pack: coef");
-            TRY_CUDA(cudaMalloc(&m->coef_bf16, sizeof(uint16_t) * (size_t)m->C_pad * m->n_pad), "pack: coef bf16");
+            const int planes = dtype == RGBD_DT_BF16X3 ? 2 : 1;
+            TRY_CUDA(cudaMalloc(&m->coef_bf16, sizeof(uint16_t) * planes * (size_t)m->C_pad * m->n_pad),
+                     "pack: coef bf16");
             TRY_CUDA(cudaMalloc(&m->asum, sizeof(float) * (size_t)m->C), "pack: asum");
-            coef_pad_kernel<<<512, 256, 0, s>>>(coef, m->C, n_sv, m->n_pad, m->C_pad, m->coef, m->coef_bf16);
+            coef_pad_kernel<<<512, 256, 0, s>>>(coef, m->C, n_sv, m->n_pad, m->C_pad, m->coef, m->coef_bf16,
+                                                dtype == RGBD_DT_BF16X3);
             TRY_CUDA(cudaGetLastError(), "pack: coef launch");
             asum_kernel<<<(m->C + 7) / 8, 256, 0, s>>>(coef, m->C, n_sv, m->asum);
             TRY_CUDA(cudaGetLastError(), "pack: asum launch");

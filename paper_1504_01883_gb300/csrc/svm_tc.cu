@@ -52,14 +52,16 @@ enum { MODE_SINGLE = 0,   // one CTA per (row block, split)
 
 // Shared-memory layout of a mode: main ring, coefficient ring (2 slots), barriers.  (The F
 // operand of the second MMA lives in tensor memory.)
-template <int MODE>
+// SPLIT2: split bf16 with the second product split too (hi and lo coefficient chunks per slot).
+template <int MODE, bool SPLIT2 = false>
 struct Lay {
-    static constexpr int STAGES = MODE == MODE_PAIR ? 6 : 4;
+    static constexpr int STAGES = MODE == MODE_PAIR ? 6 : (SPLIT2 ? 3 : 4);
     static constexpr int SV_BYTES = MODE == MODE_PAIR ? SV_TILE / 2 : SV_TILE;  // SV rows per stage
     static constexpr int STAGE = X_TILE + SV_BYTES;
     static constexpr int COEF_CHUNK = MODE == MODE_PAIR ? COEF_CHUNK_MAX / 2 : COEF_CHUNK_MAX;
+    static constexpr int COEF_SLOT = SPLIT2 ? 2 * COEF_CHUNK : COEF_CHUNK;  // hi, then lo
     static constexpr int COEF_OFF = STAGES * STAGE;
-    static constexpr int BAR_OFF = COEF_OFF + 2 * COEF_CHUNK;
+    static constexpr int BAR_OFF = COEF_OFF + 2 * COEF_SLOT;
     static constexpr int SMEM = BAR_OFF + 256 + 1024;  // + barriers + alignment slack
     static_assert(STAGES <= MAX_STAGES, "barrier slots");
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
@@ -67,7 +69,8 @@ struct Lay {
 constexpr int NUM_WARPS = 11;
 constexpr int NUM_THREADS = NUM_WARPS * 32;
 // Tensor memory: G at column 0 (256 columns), D at 256 (C_pad <= 128 columns), the two F slots
-// (128 rows x 64 bf16, packed in pairs: 32 columns each) at 384 and 416.
+// (128 rows x 64 bf16, packed in pairs: 32 columns each) at 384 and 416 -- or, with the second
+// product split, two slots of 64 columns (hi, then lo) at 384 and 448.
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t TMEM_D = 256;
 constexpr uint32_t TMEM_F = 384;
@@ -259,7 +262,8 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;             // 128-byte swizzle
     return d;
 }
-// KIND: 0 = kind::f16 (bf16 operands), 1 = kind::f8f6f4 (E4M3), 2 = kind::tf32.
+// KIND: 0 = kind::f16 (bf16 operands), 1 = kind::f8f6f4 (E4M3), 2 = kind::tf32, 3 = kind::f16 with
+// split bf16 operands (three passes, and the second product split as well).
 template <int CG, int KIND>
 __device__ __forceinline__ void mma_issue(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
 #define RGBD_MMA_SS(CGS, KS)                                                                          \
@@ -267,11 +271,11 @@ __device__ __forceinline__ void mma_issue(uint32_t d, uint64_t a, uint64_t b, ui
                  "tcgen05.mma.cta_group::" CGS ".kind::" KS " [%0], %1, %2, %3, p;\n\t}" ::"r"(d), "l"(a), \
                  "l"(b), "r"(idesc), "r"(acc))
     if constexpr (CG == 1) {
-        if constexpr (KIND == 0) RGBD_MMA_SS("1", "f16");
+        if constexpr (KIND == 0 || KIND == 3) RGBD_MMA_SS("1", "f16");
         else if constexpr (KIND == 1) RGBD_MMA_SS("1", "f8f6f4");
         else RGBD_MMA_SS("1", "tf32");
     } else {
-        if constexpr (KIND == 0) RGBD_MMA_SS("2", "f16");
+        if constexpr (KIND == 0 || KIND == 3) RGBD_MMA_SS("2", "f16");
         else if constexpr (KIND == 1) RGBD_MMA_SS("2", "f8f6f4");
         else RGBD_MMA_SS("2", "tf32");
     }
@@ -351,10 +355,13 @@ template <int MODE, int KIND>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     rbf_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_sv,
                   const __grid_constant__ CUtensorMap tm_coef, const __grid_constant__ CUtensorMap tm_x2,
-                  const __grid_constant__ CUtensorMap tm_sv2, const TcParams p) {
+                  const __grid_constant__ CUtensorMap tm_sv2, const __grid_constant__ CUtensorMap tm_coef2,
+                  const TcParams p) {
     constexpr bool MC = MODE == MODE_MC, PAIR = MODE == MODE_PAIR;
+    constexpr bool SPLIT2 = KIND == 3;
     constexpr int CG = PAIR ? 2 : 1;
-    using L = Lay<MODE>;
+    constexpr uint32_t F_SLOT = SPLIT2 ? 64u : 32u;  // TMEM columns per F slot
+    using L = Lay<MODE, SPLIT2>;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned for the 128B swizzle atoms
@@ -491,13 +498,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     break;
                 }
                 const int n0 = (t0 + (q >> 2)) * BN + (q & 3) * 64;
-                const uint32_t dst = base + L::COEF_OFF + slot * L::COEF_CHUNK;
+                const uint32_t dst = base + L::COEF_OFF + slot * L::COEF_SLOT;
+                const uint32_t nb = (SPLIT2 ? 2u : 1u) * coef_chunk_bytes;
                 if (PAIR) {
-                    if (crank == 0) bar_arrive_tx(bar(B_FFULL + slot), 2u * coef_chunk_bytes);
-                    tma_load_2d_pair(dst, &tm_coef, n0, (int)crank * (p.C_pad / 2), map_rank0(bar(B_FFULL + slot)));
+                    const uint32_t fb = map_rank0(bar(B_FFULL + slot));
+                    if (crank == 0) bar_arrive_tx(bar(B_FFULL + slot), 2u * nb);
+                    tma_load_2d_pair(dst, &tm_coef, n0, (int)crank * (p.C_pad / 2), fb);
+                    if (SPLIT2) tma_load_2d_pair(dst + L::COEF_CHUNK, &tm_coef2, n0, (int)crank * (p.C_pad / 2), fb);
                 } else {
-                    bar_arrive_tx(bar(B_FFULL + slot), coef_chunk_bytes);
+                    bar_arrive_tx(bar(B_FFULL + slot), nb);
                     tma_load_2d(dst, &tm_coef, n0, 0, bar(B_FFULL + slot));
+                    if (SPLIT2) tma_load_2d(dst + L::COEF_CHUNK, &tm_coef2, n0, 0, bar(B_FFULL + slot));
                 }
                 armed |= 1u << slot;
                 armed_par = (armed_par & ~(1u << slot)) | ((uint32_t)((q >> 1) & 1) << slot);
@@ -527,9 +538,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 tc_fence_after();
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {  // K = 16 per MMA: 8 packed columns of F
-                    const uint32_t a = tmem + TMEM_F + 32u * slot + 8u * ks;
-                    const uint64_t b = sdesc(base + L::COEF_OFF + slot * L::COEF_CHUNK + ks * 32);
-                    mma_issue_ts<CG>(d_tmem, a, b, p.idesc_second, (q_next > 0 || ks > 0) ? 1u : 0u);
+                    const uint32_t a = tmem + TMEM_F + F_SLOT * slot + 8u * ks;
+                    const uint32_t cb = base + L::COEF_OFF + slot * L::COEF_SLOT + ks * 32;
+                    mma_issue_ts<CG>(d_tmem, a, sdesc(cb), p.idesc_second, (q_next > 0 || ks > 0) ? 1u : 0u);
+                    if (SPLIT2) {  // + F_hi a_lo + F_lo a_hi
+                        mma_issue_ts<CG>(d_tmem, a, sdesc(cb + L::COEF_CHUNK), p.idesc_second, 1u);
+                        mma_issue_ts<CG>(d_tmem, a + 32u, sdesc(cb), p.idesc_second, 1u);
+                    }
                 }
                 if (PAIR)
                     tc_commit2_mc(bar(B_FEMPTY + slot), (uint16_t)0x3);
@@ -681,7 +696,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int h = 0; h < 2; ++h) {
                 const int c = set + 2 * h;  // chunk within the tile
                 const int q = 4 * u + c;    // chunk index within the split
-                uint32_t pk[32];
+                uint32_t pk[32], pl[SPLIT2 ? 32 : 1];
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     uint32_t v[32];
@@ -692,9 +707,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         const int col = n0 + c * 64 + half * 32 + j;
                         const float d0 = xs + __ldg(p.svsq + col) - 2.f * p.gscale * __uint_as_float(v[j]);
                         const float d1 = xs + __ldg(p.svsq + col + 1) - 2.f * p.gscale * __uint_as_float(v[j + 1]);
-                        const __nv_bfloat162 hv = __floats2bfloat162_rn(expm1_near0(-p.gamma * (d0 - r)),
-                                                                        expm1_near0(-p.gamma * (d1 - r)));
+                        const float f0 = expm1_near0(-p.gamma * (d0 - r)), f1 = expm1_near0(-p.gamma * (d1 - r));
+                        const __nv_bfloat162 hv = __floats2bfloat162_rn(f0, f1);
                         pk[half * 16 + (j >> 1)] = *reinterpret_cast<const uint32_t*>(&hv);
+                        if (SPLIT2) {  // lo = bf16(F - hi)
+                            const __nv_bfloat162 lv = __floats2bfloat162_rn(f0 - __low2float(hv), f1 - __high2float(hv));
+                            pl[SPLIT2 ? half * 16 + (j >> 1) : 0] = *reinterpret_cast<const uint32_t*>(&lv);
+                        }
                     }
                 }
                 if (h == 1) {  // this set's last read of G for the tile
@@ -712,8 +731,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     alive = false;
                     break;
                 }
-                // F of this warp's 32 rows into the slot's 32 columns (row = TMEM lane)
-                TC_ST_X32(tmem + lane_addr + TMEM_F + 32u * (uint32_t)set, pk);
+                // F of this warp's 32 rows into the slot's 32 columns (row = TMEM lane); the lo
+                // part into the next 32 when the second product is split
+                TC_ST_X32(tmem + lane_addr + TMEM_F + F_SLOT * (uint32_t)set, pk);
+                if constexpr (SPLIT2) TC_ST_X32(tmem + lane_addr + TMEM_F + F_SLOT * (uint32_t)set + 32u, pl);
                 tc_wait_st();
                 tc_fence_before();
                 __syncwarp();
@@ -830,6 +851,17 @@ int pack_model_tensor_maps(rgbd_svm* m) {
                         (uint64_t)m->C_pad, (uint64_t)m->n_pad * 2, 64u, (uint32_t)m->C_pad / 2,
                         CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
+    // split bf16: the lo plane of the coefficients follows the hi plane (else the hi maps again)
+    const uint16_t* coef_lo = m->coef_bf16;
+    if (m->dtype == RGBD_DT_BF16X3) coef_lo += (size_t)m->C_pad * m->n_pad;
+    rc = encode_tmap_2d(&m->tm_coef_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, coef_lo, (uint64_t)m->n_pad,
+                        (uint64_t)m->C_pad, (uint64_t)m->n_pad * 2, 64u, (uint32_t)m->C_pad,
+                        CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    rc = encode_tmap_2d(&m->tm_coef_lo_half, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, coef_lo, (uint64_t)m->n_pad,
+                        (uint64_t)m->C_pad, (uint64_t)m->n_pad * 2, 64u, (uint32_t)m->C_pad / 2,
+                        CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
     m->has_tmaps = true;
     return RGBD_OK;
 }
@@ -864,6 +896,7 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
         pl->dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     }
     pl->passes = (m->dtype == RGBD_DT_BF16X3) ? 3 : 1;
+    if (m->dtype == RGBD_DT_BF16X3) pl->kind = 3;  // split bf16, second product split too
     pl->mt = (n + BM - 1) / BM;
     pl->nt = m->n_pad / BN;
     pl->splits = ctx->tune_tc_splits > 0 ? std::min(ctx->tune_tc_splits, pl->nt)
@@ -882,12 +915,13 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
 template <int MODE, int KIND>
 cudaError_t launch_mode(const TcPlan& pl, const TcParams& p, const rgbd_svm* m, const CUtensorMap& tm_x,
                         const CUtensorMap& tm_x2, cudaStream_t s) {
-    constexpr int smem = Lay<MODE>::SMEM;
+    constexpr int smem = Lay<MODE, KIND == 3>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(rbf_tc_kernel<MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (MODE == MODE_SINGLE) {
         dim3 grid(pl.mt, pl.splits);
-        rbf_tc_kernel<MODE, KIND><<<grid, NUM_THREADS, smem, s>>>(tm_x, m->tm_sv, m->tm_coef, tm_x2, m->tm_sv_lo, p);
+        rbf_tc_kernel<MODE, KIND><<<grid, NUM_THREADS, smem, s>>>(tm_x, m->tm_sv, m->tm_coef, tm_x2, m->tm_sv_lo,
+                                                                  m->tm_coef_lo, p);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -903,7 +937,8 @@ cudaError_t launch_mode(const TcPlan& pl, const TcParams& p, const rgbd_svm* m, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, rbf_tc_kernel<MODE, KIND>, tm_x, m->tm_sv_half,
-                              MODE == MODE_PAIR ? m->tm_coef_half : m->tm_coef, tm_x2, m->tm_sv_lo_half, p);
+                              MODE == MODE_PAIR ? m->tm_coef_half : m->tm_coef, tm_x2, m->tm_sv_lo_half,
+                              MODE == MODE_PAIR ? m->tm_coef_lo_half : m->tm_coef_lo, p);
 }
 
 int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n, float x_scale,
@@ -947,16 +982,19 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     p.idesc_second = make_idesc(1, 1, mma_m, m->C_pad);
     p.passes = pl.passes;
     cudaError_t e;
-    switch (mode * 3 + pl.kind) {
-        case MODE_SINGLE * 3 + 0: e = launch_mode<MODE_SINGLE, 0>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_SINGLE * 3 + 1: e = launch_mode<MODE_SINGLE, 1>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_SINGLE * 3 + 2: e = launch_mode<MODE_SINGLE, 2>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_MC * 3 + 0: e = launch_mode<MODE_MC, 0>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_MC * 3 + 1: e = launch_mode<MODE_MC, 1>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_MC * 3 + 2: e = launch_mode<MODE_MC, 2>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_PAIR * 3 + 0: e = launch_mode<MODE_PAIR, 0>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_PAIR * 3 + 1: e = launch_mode<MODE_PAIR, 1>(pl, p, m, tm_x, tm_x2, s); break;
-        default: e = launch_mode<MODE_PAIR, 2>(pl, p, m, tm_x, tm_x2, s); break;
+    switch (mode * 4 + pl.kind) {
+        case MODE_SINGLE * 4 + 0: e = launch_mode<MODE_SINGLE, 0>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_SINGLE * 4 + 1: e = launch_mode<MODE_SINGLE, 1>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_SINGLE * 4 + 2: e = launch_mode<MODE_SINGLE, 2>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_SINGLE * 4 + 3: e = launch_mode<MODE_SINGLE, 3>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_MC * 4 + 0: e = launch_mode<MODE_MC, 0>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_MC * 4 + 1: e = launch_mode<MODE_MC, 1>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_MC * 4 + 2: e = launch_mode<MODE_MC, 2>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_MC * 4 + 3: e = launch_mode<MODE_MC, 3>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_PAIR * 4 + 0: e = launch_mode<MODE_PAIR, 0>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_PAIR * 4 + 1: e = launch_mode<MODE_PAIR, 1>(pl, p, m, tm_x, tm_x2, s); break;
+        case MODE_PAIR * 4 + 2: e = launch_mode<MODE_PAIR, 2>(pl, p, m, tm_x, tm_x2, s); break;
+        default: e = launch_mode<MODE_PAIR, 3>(pl, p, m, tm_x, tm_x2, s); break;
     }
     if (e != cudaSuccess) return cuda_error(e, "svm_score: tc launch");
     return launch_reduce_scores(part, ref, pl.splits, n, m->C, m->C_pad, m->asum, m->asum_tile, pl.tps, pl.nt,
