@@ -136,6 +136,41 @@ int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear);
 int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value);
 
 /* ======================================================================================= */
+/* Depth-space region of interest of a colour-detected face (Section 2.1)                   */
+/* ======================================================================================= */
+
+/* Depth-to-colour pixel mapping: a stand-in for the camera SDK's per-pixel mapping, exact in
+ * integers.  A depth pixel (column j, row i) holding d millimetres, d_min <= d <= d_max, maps to
+ * the colour image point
+ *   X_q = a[0]*j + a[1]*i + a[2] + (parallax / d) * 256,   Y_q = a[3]*j + a[4]*i + a[5]
+ * in Q16.16 (64-bit arithmetic; parallax / d is the integer quotient, parallax >= 0 in units of
+ * 1/256 pixel x mm: the stereo shift that grows as the object comes nearer), i.e. colour pixel
+ * (X_q >> 16, Y_q >> 16) (floor).  Depths outside [d_min, d_max] (holes included) do not map. */
+typedef struct rgbd_calib {
+    int32_t a[6];
+    int32_t parallax;
+    int32_t d_min, d_max;     /* millimetres, 1 <= d_min <= d_max */
+    int32_t colour_w, colour_h;
+} rgbd_calib;
+
+/* For each face rect detected in the colour image, the bounding rect, in depth pixels, of all
+ * depth pixels of its frame that map inside the colour image and inside that rect (Section 2.1:
+ * the depth pixels of the face are found through the camera mapping, and the rectangle bounding
+ * them is the face region of the depth image; a contour or an ellipse fitted to that point set
+ * has the same bounding rect).
+ *   depth        uint16 [n_frames][H][W] (device)
+ *   calib        host pointer, copied at the call
+ *   colour_rects rgbd_rect [n] (device): frame index and the rect in colour pixels
+ *   depth_rects  rgbd_rect [n] (device, out): (frame, x_min, y_min, x_max - x_min + 1,
+ *                y_max - y_min + 1) over the mapped pixels; (frame, 0, 0, 0, 0) when none maps
+ * A rect with frame out of range or w, h <= 0 gives (frame, 0, 0, 0, 0) and
+ * RGBD_STATUS_BAD_RECT.  Errors: RGBD_ERR_ARG (NULL pointers, sizes, a calibration with
+ * d_min < 1, d_max < d_min, parallax < 0, colour sizes <= 0, |a[0]|, |a[1]|, |a[3]|, |a[4]|
+ * above 2^24 or |a[2]|, |a[5]| above 2^30). */
+int rgbd_face_roi(rgbd_ctx* ctx, const uint16_t* depth, int n_frames, int H, int W, const rgbd_calib* calib,
+                  const rgbd_rect* colour_rects, int n, rgbd_rect* depth_rects, void* stream);
+
+/* ======================================================================================= */
 /* A1: affine crop (Section 2.1, Eq. 1 p' = x.u + y.v + t; Section 3: each face is      */
 /* resized to a fixed square)                                                              */
 /* ======================================================================================= */

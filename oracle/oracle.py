@@ -21,7 +21,7 @@ __all__ = [
     "build", "lib", "rect_coord_q16", "crop", "median_nonzero", "valid_mask", "lbp_code",
     "lbp_codes", "uniform_table", "histograms", "features_batch", "normalize_f64",
     "normalize_f32", "f32_to_bf16", "f32_to_e4m3", "e4m3_to_f64", "svm_rbf", "svm_linear",
-    "argmax", "track_nearest", "track_streams", "RECT_DTYPE", "LBP_GE", "LBP_NBR_IGNORE_MASK",
+    "argmax", "track_nearest", "track_streams", "face_roi", "CALIB_DTYPE", "RECT_DTYPE", "LBP_GE", "LBP_NBR_IGNORE_MASK",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -270,6 +270,27 @@ def argmax(scores):
 
 
 # ---- Section 2.3: nearest-centre tracking ---------------------------------------------------
+
+CALIB_DTYPE = np.dtype([("a", np.int32, 6), ("parallax", np.int32), ("d_min", np.int32), ("d_max", np.int32),
+                        ("colour_w", np.int32), ("colour_h", np.int32)])
+
+
+def face_roi(depth, calib, rects):
+    """Depth-space bounding rects of colour-detected faces (Section 2.1).  depth uint16
+    [F][H][W]; calib a CALIB_DTYPE record; rects RECT_DTYPE [n] in colour pixels."""
+    depth = np.ascontiguousarray(depth, np.uint16)
+    if depth.ndim == 2:
+        depth = depth[None]
+    F, H, W = depth.shape
+    rects = np.ascontiguousarray(rects, RECT_DTYPE)
+    cal = np.ascontiguousarray(np.asarray(calib, CALIB_DTYPE).reshape(1))
+    out = np.zeros(len(rects), RECT_DTYPE)
+    L = lib()
+    L.orc_face_roi.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    L.orc_face_roi(_p(depth), F, H, W, _p(cal), _p(rects), len(rects), _p(out))
+    return out
+
 
 def track_streams(state, frame_stream, frame_start, rects, labels):
     """Per-stream tracking over a batch (Section 2.3); `state` = dict(rects [S][M] RECT_DTYPE,

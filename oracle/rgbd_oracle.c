@@ -389,6 +389,51 @@ void orc_argmax(const double* scores, int n, int n_classes, int32_t* labels) {
  * rect centre (x + w/2, y + h/2) is nearest in Euclidean distance; -1 if the stream has no
  * current face; ties go to the lowest index.  Distances are compared in fp64 on the
  * half-pixel centres. */
+/* Depth-to-colour mapping of the face region (Section 2.1): a depth pixel (column j, row i)
+ * holding d mm, d_min <= d <= d_max, lands on colour point
+ *   X = a0 j + a1 i + a2 + 256 (parallax / d),   Y = a3 j + a4 i + a5      (Q16.16, integers)
+ * and the face's depth region is the bounding rect of the depth pixels landing inside the colour
+ * image and inside the detected colour rect. */
+typedef struct {
+    int32_t a[6];
+    int32_t parallax, d_min, d_max, colour_w, colour_h;
+} orc_calib;
+
+static int64_t floor_div_q16(int64_t v) { return v >= 0 ? v / 65536 : -((-v + 65535) / 65536); }
+
+void orc_face_roi(const uint16_t* depth, int n_frames, int H, int W, const orc_calib* c, const orc_rect* rects,
+                  int n, orc_rect* out) {
+    for (int k = 0; k < n; ++k) {
+        const orc_rect r = rects[k];
+        out[k].frame = r.frame;
+        out[k].x = out[k].y = out[k].w = out[k].h = 0;
+        if (r.frame < 0 || r.frame >= n_frames || r.w <= 0 || r.h <= 0) continue;
+        int xmin = W, ymin = H, xmax = -1, ymax = -1;
+        for (int i = 0; i < H; ++i) {
+            for (int j = 0; j < W; ++j) {
+                const int d = depth[((size_t)r.frame * H + i) * W + j];
+                if (d < c->d_min || d > c->d_max) continue;
+                const int64_t X = (int64_t)c->a[0] * j + (int64_t)c->a[1] * i + c->a[2] +
+                                  (int64_t)(c->parallax / d) * 256;
+                const int64_t Y = (int64_t)c->a[3] * j + (int64_t)c->a[4] * i + c->a[5];
+                const int64_t x = floor_div_q16(X), y = floor_div_q16(Y);
+                if (x < 0 || x >= c->colour_w || y < 0 || y >= c->colour_h) continue;
+                if (x < r.x || x >= (int64_t)r.x + r.w || y < r.y || y >= (int64_t)r.y + r.h) continue;
+                if (j < xmin) xmin = j;
+                if (j > xmax) xmax = j;
+                if (i < ymin) ymin = i;
+                if (i > ymax) ymax = i;
+            }
+        }
+        if (xmax >= 0) {
+            out[k].x = xmin;
+            out[k].y = ymin;
+            out[k].w = xmax - xmin + 1;
+            out[k].h = ymax - ymin + 1;
+        }
+    }
+}
+
 void orc_track_nearest(const orc_rect* prev, int n_prev, const orc_rect* cur, int n_cur, int32_t* match) {
     for (int i = 0; i < n_prev; ++i) {
         double px = prev[i].x + prev[i].w / 2.0, py = prev[i].y + prev[i].h / 2.0;

@@ -79,6 +79,7 @@ def lib():
             "rgbd_ctx_set_tuning": [P, I, I],
             "rgbd_track_nearest": [P, P, I, P, I, P, P],
             "rgbd_debug_expm1": [P, P, I, P],
+            "rgbd_face_roi": [P, P, I, I, I, P, P, I, P, P],
             "rgbd_track_streams": [P, P, P, P, I, I, I, P, P, P, I, P, P, P],
         }
         for name, args in sig.items():
@@ -228,6 +229,34 @@ def rgbd_track_nearest(ctx, prev, cur, match=None, stream=None):
     _check(lib().rgbd_track_nearest(ctx.handle, _p(prev), n_prev, _p(cur) if n_cur else None, n_cur, _p(match),
                                     _stream(stream)))
     return match
+
+
+class Calib(ctypes.Structure):
+    """rgbd_calib: depth-to-colour mapping (see rgbd_face_roi)."""
+    _fields_ = [("a", ctypes.c_int32 * 6), ("parallax", ctypes.c_int32), ("d_min", ctypes.c_int32),
+                ("d_max", ctypes.c_int32), ("colour_w", ctypes.c_int32), ("colour_h", ctypes.c_int32)]
+
+    @classmethod
+    def from_record(cls, rec):
+        """From a record with fields a[6], parallax, d_min, d_max, colour_w, colour_h."""
+        c = cls()
+        for i in range(6):
+            c.a[i] = int(rec["a"][i])
+        for f in ("parallax", "d_min", "d_max", "colour_w", "colour_h"):
+            setattr(c, f, int(rec[f]))
+        return c
+
+
+def rgbd_face_roi(ctx, depth, calib, colour_rects, out=None, stream=None):
+    """Depth-space rects of colour-detected faces (Section 2.1).  depth int16/uint16 [F][H][W]
+    (CUDA), calib a Calib, colour_rects int32 [n][5] (CUDA).  Returns int32 [n][5]."""
+    F, H, W = depth.shape
+    n = colour_rects.shape[0]
+    if out is None:
+        out = torch.empty((n, 5), dtype=torch.int32, device=depth.device)
+    _check(lib().rgbd_face_roi(ctx.handle, _p(depth), F, H, W, ctypes.addressof(calib), _p(colour_rects) if n else None,
+                               n, _p(out) if n else None, _stream(stream)))
+    return out
 
 
 class TrackState:

@@ -160,6 +160,42 @@ def frames_with_rects(seed, n_frames, per_frame, smin, smax, H=FRAME_H, W=FRAME_
 
 
 # ---------------------------------------------------------------------------------------------
+# Depth-to-colour calibration and colour-image face boxes (inputs of the region-of-interest step)
+# ---------------------------------------------------------------------------------------------
+
+CALIB_FIELDS = np.dtype([("a", np.int32, 6), ("parallax", np.int32), ("d_min", np.int32), ("d_max", np.int32),
+                         ("colour_w", np.int32), ("colour_h", np.int32)])
+
+
+def calibration(rng, colour_w=FRAME_W, colour_h=FRAME_H):
+    """Parameters of a depth-to-colour pixel mapping standing in for an RGB-D camera's: scale
+    1 +- 3 %, shear up to 1 %, offsets up to 8 px (all Q16.16), a stereo shift of 20-30 px at
+    1 m (in 1/256 px x mm) and a valid range of 400-8000 mm."""
+    c = np.zeros((), CALIB_FIELDS)
+    c["a"] = [int(65536 * rng.uniform(0.97, 1.03)), int(65536 * rng.uniform(-0.01, 0.01)),
+              int(65536 * rng.uniform(-8, 8)), int(65536 * rng.uniform(-0.01, 0.01)),
+              int(65536 * rng.uniform(0.97, 1.03)), int(65536 * rng.uniform(-8, 8))]
+    c["parallax"] = int(rng.uniform(20, 30) * 1000 * 256)
+    c["d_min"], c["d_max"] = 400, 8000
+    c["colour_w"], c["colour_h"] = colour_w, colour_h
+    return c
+
+
+def colour_boxes(rng, rects):
+    """Detector boxes in the colour image for faces drawn under `rects` (depth pixels): shifted
+    right by 15-35 px (the stereo offset at face distance) and by up to 5 px vertically, side
+    within 5 %."""
+    out = rects.copy()
+    n = len(rects)
+    out["x"] = rects["x"] + rng.integers(15, 36, n)
+    out["y"] = rects["y"] + rng.integers(-5, 6, n)
+    side = np.maximum(8, np.rint(rects["w"] * rng.uniform(0.95, 1.05, n))).astype(np.int32)
+    out["w"] = side
+    out["h"] = side
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
 # SVM models and histogram-like count rows
 # ---------------------------------------------------------------------------------------------
 

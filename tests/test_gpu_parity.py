@@ -359,3 +359,31 @@ def test_track_streams_against_oracle(B, ctx, orc):
         got_r = state.rects.cpu().numpy()[s, :c]
         for k, f in enumerate(["frame", "x", "y", "w", "h"]):
             assert (got_r[:, k] == ref["rects"][f][s, :c]).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# Section 2.1: depth-space region of a colour-detected face
+# ---------------------------------------------------------------------------------------------
+
+def test_face_roi_against_oracle(B, ctx, orc):
+    """Synthetic frames, calibrations and colour boxes (plus rects outside the colour image,
+    partly outside, tiny, with a bad frame index and a degenerate calibration): the depth rects
+    equal the oracle's full-frame scan exactly."""
+    rng = synth.rng_for(41)
+    grey, depth, rects = synth.frames_with_rects(41, 3, 5, 48, 256)
+    boxes = synth.colour_boxes(rng, rects)
+    extra = np.array([(0, 700, 10, 40, 40), (1, -30, -30, 50, 50), (2, 300, 200, 1, 1), (5, 10, 10, 20, 20),
+                      (0, 10, 10, 0, 20)], orc.RECT_DTYPE)
+    boxes = np.concatenate([boxes, extra])
+    d_dev = torch.from_numpy(depth.view(np.int16)).cuda()
+    for k in range(4):
+        cal = synth.calibration(rng)
+        if k == 3:  # a mapping that collapses the y axis: the kernel scans the whole frame
+            cal["a"][3], cal["a"][4] = 0, 0
+        want = orc.face_roi(depth, cal, boxes)
+        got = B.rgbd_face_roi(ctx, d_dev, B.Calib.from_record(cal), B.rects_tensor(boxes)).cpu().numpy()
+        for i, f in enumerate(["frame", "x", "y", "w", "h"]):
+            assert (got[:, i] == want[f]).all(), (k, f)
+        if k == 0:
+            assert (want["w"][:15] > 0).all()  # the synthetic faces are found
+        ctx.status(clear=True)

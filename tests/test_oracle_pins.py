@@ -456,3 +456,91 @@ def test_track_streams_brute_force(orc):
             keep = min(k1 - k0, M)
             ref[s] = ([(cx[i], cy[i]) for i in range(keep)], [int(want[k0 + i]) for i in range(keep)])
         assert (got == want).all()
+
+
+def _calib(orc, a, parallax=0, d_min=1, d_max=65535, cw=640, ch=480):
+    c = np.zeros((), orc.CALIB_DTYPE)
+    c["a"] = a
+    c["parallax"], c["d_min"], c["d_max"], c["colour_w"], c["colour_h"] = parallax, d_min, d_max, cw, ch
+    return c
+
+
+def test_face_roi_hand_cases(orc):
+    """Section 2.1: the depth pixels that map into the colour rect, and their bounding rect."""
+    R = orc.RECT_DTYPE
+    ident = [65536, 0, 0, 0, 65536, 0]
+    d = np.full((6, 8), 1000, np.uint16)
+    d[2, 1] = 0          # hole inside the rect
+    d[4, 4] = 0
+    # identity mapping: colour rect x 1..4, y 2..4 -> the same depth pixels; holes at the rect's
+    # corners do not shrink it while other pixels of that row / column remain
+    out = orc.face_roi(d, _calib(orc, ident, cw=8, ch=6), np.array([(0, 1, 2, 4, 3)], R))
+    assert tuple(out[0]) == (0, 1, 2, 4, 3)
+    # remove the whole column x = 1 of the rect: the box starts at x = 2
+    d2 = d.copy()
+    d2[2:5, 1] = 0
+    out = orc.face_roi(d2, _calib(orc, ident, cw=8, ch=6), np.array([(0, 1, 2, 4, 3)], R))
+    assert tuple(out[0]) == (0, 2, 2, 3, 3)
+    # parallax: 20 px at 1000 mm (20 * 1000 * 256 in 1/256 px mm) shifts colour x by +20, so the
+    # colour rect x 30..39 is depth x 10..19
+    d3 = np.full((20, 40), 1000, np.uint16)
+    c = _calib(orc, ident, parallax=20 * 1000 * 256)
+    out = orc.face_roi(d3, c, np.array([(0, 30, 5, 10, 4)], R))
+    assert tuple(out[0]) == (0, 10, 5, 10, 4)
+    # at 2000 mm the shift halves: colour 30..39 is depth 20..29 (clipped to the 40-wide frame)
+    d4 = np.full((20, 40), 2000, np.uint16)
+    out = orc.face_roi(d4, c, np.array([(0, 30, 5, 10, 4)], R))
+    assert tuple(out[0]) == (0, 20, 5, 10, 4)
+    # depth range: pixels nearer than d_min do not map
+    c2 = _calib(orc, ident, parallax=20 * 1000 * 256, d_min=1500)
+    out = orc.face_roi(d3, c2, np.array([(0, 30, 5, 10, 4)], R))
+    assert tuple(out[0]) == (0, 0, 0, 0, 0)
+    # a colour image at twice the resolution: colour x = 2j, so colour 10..20 is depth 5..10
+    c3 = _calib(orc, [131072, 0, 0, 0, 131072, 0])
+    out = orc.face_roi(d3, c3, np.array([(0, 10, 4, 11, 6)], R))
+    assert tuple(out[0]) == (0, 5, 2, 6, 3)
+    # floor, not truncation: an offset of -0.5 px sends depth column 0 to colour x = -1 (outside)
+    c4 = _calib(orc, [65536, 0, -32768, 0, 65536, 0])
+    out = orc.face_roi(d3, c4, np.array([(0, 0, 0, 3, 3)], R))
+    assert tuple(out[0]) == (0, 1, 0, 3, 3)   # colour x 0..2 <- depth j 1..3
+    # bad descriptors and a rect outside the colour image
+    out = orc.face_roi(d3, c, np.array([(1, 0, 0, 5, 5), (0, 0, 0, 0, 5), (0, 900, 0, 5, 5)], R))
+    assert [tuple(o) for o in out] == [(1, 0, 0, 0, 0), (0, 0, 0, 0, 0), (0, 0, 0, 0, 0)]
+
+
+def test_face_roi_brute_force(orc):
+    """Random frames and calibrations (shear, scale, offset, parallax) against a vectorised
+    numpy restatement of the mapping."""
+    R = orc.RECT_DTYPE
+    rng = np.random.default_rng(31)
+    for it in range(10):
+        F, H, W = 2, int(rng.integers(10, 40)), int(rng.integers(10, 50))
+        d = rng.integers(300, 5000, (F, H, W)).astype(np.uint16)
+        d[rng.random((F, H, W)) < 0.1] = 0
+        a = [int(rng.integers(40000, 90000)), int(rng.integers(-9000, 9000)), int(rng.integers(-300000, 300000)),
+             int(rng.integers(-9000, 9000)), int(rng.integers(40000, 90000)), int(rng.integers(-300000, 300000))]
+        c = _calib(orc, a, parallax=int(rng.integers(0, 30 * 1000 * 256)), d_min=400, d_max=4500,
+                   cw=int(rng.integers(20, 60)), ch=int(rng.integers(15, 45)))
+        rects = np.zeros(6, R)
+        rects["frame"] = rng.integers(0, F, 6)
+        rects["x"] = rng.integers(-5, 50, 6)
+        rects["y"] = rng.integers(-5, 40, 6)
+        rects["w"] = rng.integers(1, 30, 6)
+        rects["h"] = rng.integers(1, 30, 6)
+        got = orc.face_roi(d, c, rects)
+        ii, jj = np.meshgrid(np.arange(H, dtype=np.int64), np.arange(W, dtype=np.int64), indexing="ij")
+        for k, r in enumerate(rects):
+            dd = d[r["frame"]].astype(np.int64)
+            ok = (dd >= 400) & (dd <= 4500)
+            par = np.where(ok, c["parallax"] // np.maximum(dd, 1), 0) * 256
+            X = a[0] * jj + a[1] * ii + a[2] + par
+            Y = a[3] * jj + a[4] * ii + a[5]
+            x, y = np.floor_divide(X, 65536), np.floor_divide(Y, 65536)
+            m = ok & (x >= 0) & (x < c["colour_w"]) & (y >= 0) & (y < c["colour_h"])
+            m &= (x >= r["x"]) & (x < r["x"] + r["w"]) & (y >= r["y"]) & (y < r["y"] + r["h"])
+            if not m.any():
+                assert tuple(got[k])[1:] == (0, 0, 0, 0)
+                continue
+            ys, xs = np.nonzero(m)
+            assert tuple(got[k]) == (r["frame"], xs.min(), ys.min(), xs.max() - xs.min() + 1,
+                                     ys.max() - ys.min() + 1), it
