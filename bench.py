@@ -215,7 +215,7 @@ def main():
                     help="fixed launch layout (K1 CTAs/SM, scoring splits, CTA pairing 1=multicast 2=none "
                          "3=2-CTA MMA) instead of the autotuner, e.g. to profile the layout a previous run chose")
     ap.add_argument("--ref-crops-per-step", type=int, default=8)
-    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision", "roi"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision", "roi", "train"],
                     help="batch: the headline line; the others measure the remaining workloads")
     ap.add_argument("--seconds", type=float, default=10.0, help="serving: simulated seconds of arrivals")
     args = ap.parse_args()

@@ -285,6 +285,32 @@ int svm_score(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* 
               float x_scale, float* scores, int32_t* labels, void* stream);
 
 /* ======================================================================================= */
+/* SVM training (Section 2.5; the paper trains on the host)                                 */
+/* ======================================================================================= */
+
+/* One-vs-rest RBF SVM training of n_classes classifiers on the same n rows.  For class c,
+ * y_t = +1 if labels[t] == c else -1, and with K_st = exp(-gamma |x_s - x_t|^2) the dual problem
+ *   minimise 1/2 sum_st alpha_s alpha_t y_s y_t K_st - sum_t alpha_t,
+ *   0 <= alpha_t <= cost, sum_t y_t alpha_t = 0
+ * is solved by sequential minimal optimisation: each step takes the maximal violating pair
+ * (i = argmax over the indices that may move up of -y_t G_t, j = argmin over those that may move
+ * down, lowest index on ties; G the gradient), stops when the gap is at most eps or after
+ * max_iter steps, and otherwise moves the pair along the constraint by the clipped Newton step.
+ * The bias makes y_t f(x_t) = 1 on average over the free vectors (0 < alpha < cost), else it is
+ * the midpoint of the last bounds.
+ *   x        float [n][k_pad] normalised rows (lbp_normalize_features with RGBD_DT_F32)
+ *   xsq      float [n] their squared norms
+ *   labels   int32 [n], values in 0..n_classes-1 (others train as "rest" in every class)
+ *   coef     float [n_classes][n] out: a_ct = y_t alpha_t (svm_train_data_pack's coefficients)
+ *   bias     float [n_classes] out: b_c, so that f_c(x) = sum_t a_ct K(x_t, x) + b_c
+ *   iters    int32 [n_classes] out: SMO steps taken (max_iter means the gap was not reached)
+ * The kernel matrix (4 n^2 bytes, fp32) lives in the context workspace; n is 2..16384,
+ * max_iter 0..2e6.  Asynchronous on stream.  Errors: RGBD_ERR_ARG, RGBD_ERR_NOMEM. */
+int svm_train_rbf(rgbd_ctx* ctx, const float* x, const float* xsq, int n, int k_pad, const int32_t* labels,
+                  int n_classes, float gamma, float cost, float eps, int max_iter, float* coef, float* bias,
+                  int32_t* iters, void* stream);
+
+/* ======================================================================================= */
 /* Nearest-centre face tracking (Section 2.3)                                              */
 /* ======================================================================================= */
 

@@ -21,7 +21,7 @@ __all__ = [
     "build", "lib", "rect_coord_q16", "crop", "median_nonzero", "valid_mask", "lbp_code",
     "lbp_codes", "uniform_table", "histograms", "features_batch", "normalize_f64",
     "normalize_f32", "f32_to_bf16", "f32_to_e4m3", "e4m3_to_f64", "svm_rbf", "svm_linear",
-    "argmax", "track_nearest", "track_streams", "face_roi", "CALIB_DTYPE", "RECT_DTYPE", "LBP_GE", "LBP_NBR_IGNORE_MASK",
+    "argmax", "track_nearest", "track_streams", "face_roi", "CALIB_DTYPE", "svm_train_rbf", "RECT_DTYPE", "LBP_GE", "LBP_NBR_IGNORE_MASK",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -270,6 +270,23 @@ def argmax(scores):
 
 
 # ---- Section 2.3: nearest-centre tracking ---------------------------------------------------
+
+def svm_train_rbf(x64, labels, n_classes, gamma, cost=1.0, eps=1e-3, max_iter=100000):
+    """One-vs-rest RBF SVM by SMO (maximal violating pair) in fp64.  x64 float64 [n][dim] (the
+    normalised rows).  Returns (a [C][n] = y * alpha, b [C], iterations [C])."""
+    x64 = np.ascontiguousarray(x64, np.float64)
+    n, dim = x64.shape
+    lab = np.ascontiguousarray(labels, np.int32)
+    a = np.zeros((n_classes, n), np.float64)
+    b = np.zeros(n_classes, np.float64)
+    it = np.zeros(n_classes, np.int32)
+    L = lib()
+    L.orc_svm_train_rbf.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.orc_svm_train_rbf(_p(x64), n, dim, _p(lab), n_classes, gamma, cost, eps, max_iter, _p(a), _p(b), _p(it))
+    return a, b, it
+
 
 CALIB_DTYPE = np.dtype([("a", np.int32, 6), ("parallax", np.int32), ("d_min", np.int32), ("d_max", np.int32),
                         ("colour_w", np.int32), ("colour_h", np.int32)])

@@ -389,6 +389,110 @@ void orc_argmax(const double* scores, int n, int n_classes, int32_t* labels) {
  * rect centre (x + w/2, y + h/2) is nearest in Euclidean distance; -1 if the stream has no
  * current face; ties go to the lowest index.  Distances are compared in fp64 on the
  * half-pixel centres. */
+/* One-vs-rest RBF SVM training (Section 2.5 trains the classifier on the face database; here
+ * the dual problem is solved by sequential minimal optimisation with the maximal violating pair).
+ * For class c, y_t = +1 if labels[t] == c else -1, and with K_st = exp(-gamma |x_s - x_t|^2):
+ *   minimise f(alpha) = 1/2 sum_st alpha_s alpha_t y_s y_t K_st - sum_t alpha_t
+ *   subject to 0 <= alpha_t <= cost, sum_t y_t alpha_t = 0.
+ * G_t = y_t sum_s alpha_s y_s K_st - 1 is the gradient.  Each step takes
+ *   i = argmax_{t in I_up} -y_t G_t,   j = argmin_{t in I_low} -y_t G_t
+ * (I_up: y = +1 and alpha < cost, or y = -1 and alpha > 0; I_low: y = +1 and alpha > 0, or
+ * y = -1 and alpha < cost; the lowest index on ties), stops when the gap m - M <= eps, and
+ * otherwise moves alpha_i += y_i lambda, alpha_j -= y_j lambda with
+ * lambda = min((m - M) / eta, the box limits), eta = K_ii + K_jj - 2 K_ij (at least 1e-12); then
+ * G_t += y_t lambda (K_it - K_jt).  The bias b makes y_t f(x_t) = 1 on the free vectors: the mean
+ * of -y_t G_t over 0 < alpha_t < cost, else the midpoint (m + M) / 2 of the last bounds (m alone,
+ * M alone, or 0 when a side is empty).  Outputs a_ct = y_t alpha_t and b_c, so that the decision
+ * function is f_c(x) = sum_t a_ct K(x_t, x) + b_c, and the steps taken per class. */
+void orc_svm_train_rbf(const double* x, int n, int dim, const int32_t* labels, int n_classes, double gamma,
+                       double cost, double eps, int max_iter, double* a_out, double* b_out, int32_t* iters) {
+    double* K = (double*)malloc(sizeof(double) * (size_t)n * n);
+    for (int s = 0; s < n; ++s)
+        for (int t = 0; t < n; ++t) {
+            double d2 = 0.0;
+            for (int k = 0; k < dim; ++k) {
+                const double df = x[(size_t)s * dim + k] - x[(size_t)t * dim + k];
+                d2 += df * df;
+            }
+            K[(size_t)s * n + t] = exp(-gamma * d2);
+        }
+    double* alpha = (double*)malloc(sizeof(double) * (size_t)n);
+    double* G = (double*)malloc(sizeof(double) * (size_t)n);
+    int* y = (int*)malloc(sizeof(int) * (size_t)n);
+    for (int c = 0; c < n_classes; ++c) {
+        for (int t = 0; t < n; ++t) {
+            y[t] = labels[t] == c ? 1 : -1;
+            alpha[t] = 0.0;
+            G[t] = -1.0;
+        }
+        int it = 0;
+        double m = 0.0, M = 0.0;
+        int have_up = 0, have_low = 0;
+        for (;;) {
+            int i = -1, j = -1;
+            for (int t = 0; t < n; ++t) {
+                const double v = -y[t] * G[t];
+                const int up = (y[t] > 0 && alpha[t] < cost) || (y[t] < 0 && alpha[t] > 0.0);
+                const int low = (y[t] > 0 && alpha[t] > 0.0) || (y[t] < 0 && alpha[t] < cost);
+                if (up && (i < 0 || v > m)) {
+                    i = t;
+                    m = v;
+                }
+                if (low && (j < 0 || v < M)) {
+                    j = t;
+                    M = v;
+                }
+            }
+            have_up = i >= 0;
+            have_low = j >= 0;
+            if (!have_up || !have_low || m - M <= eps || it >= max_iter) break;
+            double eta = K[(size_t)i * n + i] + K[(size_t)j * n + j] - 2.0 * K[(size_t)i * n + j];
+            if (eta < 1e-12) eta = 1e-12;
+            double lam = (m - M) / eta;
+            const double lim_i = y[i] > 0 ? cost - alpha[i] : alpha[i];
+            const double lim_j = y[j] > 0 ? alpha[j] : cost - alpha[j];
+            if (lam > lim_i) lam = lim_i;
+            if (lam > lim_j) lam = lim_j;
+            alpha[i] += y[i] * lam;
+            alpha[j] -= y[j] * lam;
+            /* snap the box edges exactly */
+            if (alpha[i] < 0.0) alpha[i] = 0.0;
+            if (alpha[i] > cost) alpha[i] = cost;
+            if (alpha[j] < 0.0) alpha[j] = 0.0;
+            if (alpha[j] > cost) alpha[j] = cost;
+            if (lam == lim_i) alpha[i] = y[i] > 0 ? cost : 0.0;
+            if (lam == lim_j) alpha[j] = y[j] > 0 ? 0.0 : cost;
+            for (int t = 0; t < n; ++t) G[t] += y[t] * lam * (K[(size_t)i * n + t] - K[(size_t)j * n + t]);
+            ++it;
+        }
+        double sum = 0.0;
+        int nfree = 0;
+        for (int t = 0; t < n; ++t)
+            if (alpha[t] > 0.0 && alpha[t] < cost) {
+                sum += -y[t] * G[t];
+                ++nfree;
+            }
+        double b;
+        if (nfree > 0)
+            b = sum / nfree;
+        else if (have_up && have_low)
+            b = 0.5 * (m + M);
+        else if (have_up)
+            b = m;
+        else if (have_low)
+            b = M;
+        else
+            b = 0.0;
+        for (int t = 0; t < n; ++t) a_out[(size_t)c * n + t] = y[t] * alpha[t];
+        b_out[c] = b;
+        iters[c] = it;
+    }
+    free(K);
+    free(alpha);
+    free(G);
+    free(y);
+}
+
 /* Depth-to-colour mapping of the face region (Section 2.1): a depth pixel (column j, row i)
  * holding d mm, d_min <= d <= d_max, lands on colour point
  *   X = a0 j + a1 i + a2 + 256 (parallax / d),   Y = a3 j + a4 i + a5      (Q16.16, integers)

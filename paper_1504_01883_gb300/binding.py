@@ -80,6 +80,7 @@ def lib():
             "rgbd_track_nearest": [P, P, I, P, I, P, P],
             "rgbd_debug_expm1": [P, P, I, P],
             "rgbd_face_roi": [P, P, I, I, I, P, P, I, P, P],
+            "svm_train_rbf": [P, P, P, I, I, P, I, F, F, F, I, P, P, P, P],
             "rgbd_track_streams": [P, P, P, P, I, I, I, P, P, P, I, P, P, P],
         }
         for name, args in sig.items():
@@ -229,6 +230,18 @@ def rgbd_track_nearest(ctx, prev, cur, match=None, stream=None):
     _check(lib().rgbd_track_nearest(ctx.handle, _p(prev), n_prev, _p(cur) if n_cur else None, n_cur, _p(match),
                                     _stream(stream)))
     return match
+
+
+def svm_train_rbf(ctx, x, xsq, labels, n_classes, gamma, cost=1.0, eps=1e-3, max_iter=200000, stream=None):
+    """One-vs-rest RBF SVM training (SMO) on normalised fp32 rows x [n][k_pad] with norms xsq [n]
+    and int32 labels [n] (all CUDA).  Returns (coef [C][n], bias [C], iters [C])."""
+    n, k_pad = x.shape
+    coef = torch.empty((n_classes, n), dtype=torch.float32, device=x.device)
+    bias = torch.empty((n_classes,), dtype=torch.float32, device=x.device)
+    iters = torch.empty((n_classes,), dtype=torch.int32, device=x.device)
+    _check(lib().svm_train_rbf(ctx.handle, _p(x), _p(xsq), n, k_pad, _p(labels), n_classes, gamma, cost, eps,
+                               max_iter, _p(coef), _p(bias), _p(iters), _stream(stream)))
+    return coef, bias, iters
 
 
 class Calib(ctypes.Structure):

@@ -17,18 +17,6 @@ constexpr int kRoiThreads = 256;
 
 __device__ __forceinline__ long long floor_q16(long long v) { return v >> 16; }  // arithmetic shift = floor
 
-// floor(P / d) for 0 <= P < 2^31, 1 <= d < 2^16 by estimate and correction: fl(P) * rcp(d) has
-// a relative error below 3 * 2^-24 < 2^-22 (three round-to-nearest steps), so for quotients
-// below 2^22 its absolute error is below 1 and its truncation is the quotient or one off; one
-// exact integer step up or down then gives the quotient.  Larger quotients divide directly.
-__device__ __forceinline__ long long quot(int P, int d) {
-    if ((long long)P >= ((long long)d << 22)) return (long long)(P / d);
-    long long q = (long long)((float)P * __frcp_rn((float)d));
-    if (q * d > P) --q;
-    else if ((q + 1) * d <= P) ++q;
-    return q;
-}
-
 // One CTA per face.  The scan covers a window that holds every depth pixel which can map inside
 // the rect: with p(d) = 256 (parallax / d) between p_lo (at d_max) and p_hi (at d_min), a pixel
 // inside needs A = a0 j + a1 i + a2 in [X0 - p_hi, X1 - p_lo) and B = a3 j + a4 i + a5 in [Y0, Y1)
@@ -89,7 +77,7 @@ __global__ void __launch_bounds__(kRoiThreads) face_roi_kernel(const uint16_t* _
                     const int d = dp[(size_t)i * W + j];
                     if (d < c.d_min || d > c.d_max) continue;
                     const long long X = (long long)c.a[0] * j + (long long)c.a[1] * i + c.a[2] +
-                                        quot(c.parallax, d) * 256;
+                                        (long long)(c.parallax / d) * 256;
                     const long long Y = (long long)c.a[3] * j + (long long)c.a[4] * i + c.a[5];
                     // inside the clipped rect <=> floor(X / 2^16) in [max(x,0), min(x+w, cw)), same for Y
                     if (floor_q16(X) < X0 / 65536 || X >= X1 || floor_q16(Y) < Y0 / 65536 || Y >= Y1) continue;

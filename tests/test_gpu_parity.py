@@ -387,3 +387,47 @@ def test_face_roi_against_oracle(B, ctx, orc):
         if k == 0:
             assert (want["w"][:15] > 0).all()  # the synthetic faces are found
         ctx.status(clear=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# Section 2.5: one-vs-rest RBF SVM training (SMO) on the GPU
+# ---------------------------------------------------------------------------------------------
+
+def _class_counts(seed, n, cells, C):
+    rng = synth.rng_for(seed)
+    dim = cells * 59
+    protos = rng.uniform(0.5, 1.5, (C, dim))
+    lab = rng.integers(0, C, n).astype(np.int32)
+    counts = rng.poisson(3.0 * protos[lab]).astype(np.uint16)
+    test = rng.poisson(3.0 * protos[rng.integers(0, C, 64)]).astype(np.uint16)
+    return counts, lab, test
+
+
+def test_svm_train_against_oracle_and_scoring(B, ctx, orc):
+    """GPU SMO (fp32 kernel matrix and gradient) against the fp64 oracle on decision values of
+    unseen rows, then the trained coefficients packed and scored through svm_score."""
+    C, gamma, cost, eps = 4, 5.0, 1.0, 1e-4
+    counts, lab, test = _class_counts(61, 300, 16, C)
+    x, q = B.lbp_normalize_features(ctx, dev_u16(counts), "f32")
+    coef, bias, iters = B.svm_train_rbf(ctx, x, q, torch.from_numpy(lab).cuda(), C, gamma, cost, eps)
+    assert ctx.status() == 0
+    a, b, it = orc.svm_train_rbf(orc.normalize_f64(counts), lab, C, gamma, cost, eps=eps)
+    x64, t64 = orc.normalize_f64(counts), orc.normalize_f64(test)
+    Kt = np.exp(-gamma * ((t64[:, None, :] - x64[None, :, :]) ** 2).sum(-1))
+    f_gpu = Kt @ coef.cpu().numpy().astype(np.float64).T + bias.cpu().numpy()
+    f_orc = Kt @ a.T + b
+    assert np.abs(f_gpu - f_orc).max() < 2e-3, np.abs(f_gpu - f_orc).max()
+    assert (iters.cpu().numpy() > 0).all() and (iters.cpu().numpy() < 200000).all()
+    # box and equality constraints hold on the GPU solution
+    y = np.where(lab[None, :] == np.arange(C)[:, None], 1, -1)
+    alpha = coef.cpu().numpy() * y
+    assert (alpha >= 0).all() and (alpha <= cost * (1 + 1e-6)).all()
+    assert np.abs((coef.cpu().numpy()).sum(1)).max() < 1e-3
+    # train -> pack -> score: the library's scoring of the trained model equals its definition
+    model = B.svm_train_data_pack(ctx, dev_u16(counts), coef, bias, gamma=gamma, dtype="f32")
+    xt, qt = B.lbp_normalize_features(ctx, dev_u16(test), "f32")
+    s, labels = B.svm_score(ctx, model, xt, qt)
+    assert np.abs(s.cpu().numpy() - f_gpu).max() < 1e-4
+    srt = np.sort(f_orc, axis=1)
+    clear = (srt[:, -1] - srt[:, -2]) > 5e-3
+    assert (labels.cpu().numpy()[clear] == np.argmax(f_orc, axis=1)[clear]).all()

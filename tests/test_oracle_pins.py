@@ -544,3 +544,57 @@ def test_face_roi_brute_force(orc):
             ys, xs = np.nonzero(m)
             assert tuple(got[k]) == (r["frame"], xs.min(), ys.min(), xs.max() - xs.min() + 1,
                                      ys.max() - ys.min() + 1), it
+
+
+def test_svm_train_two_points_closed_form(orc):
+    """Two points of opposite classes: alpha = 1 / (1 - k) with k = K(x0, x1) (one SMO step),
+    b = 0 by symmetry, and the decision function is +1 / -1 on the two points."""
+    x = np.array([[0.2, 0.8, 0.0], [0.5, 0.1, 0.4]])
+    gamma = 1.3
+    k = np.exp(-gamma * ((x[0] - x[1]) ** 2).sum())
+    a, b, it = orc.svm_train_rbf(x, np.array([0, 1], np.int32), 1, gamma, cost=100.0, eps=1e-9)
+    assert it[0] == 1
+    assert abs(a[0, 0] - 1.0 / (1.0 - k)) < 1e-12 and abs(a[0, 1] + 1.0 / (1.0 - k)) < 1e-12
+    assert abs(b[0]) < 1e-12
+    # a box that binds: alpha stops at cost, the point is not free, b from the bounds
+    a, b, it = orc.svm_train_rbf(x, np.array([0, 1], np.int32), 1, gamma, cost=0.5, eps=1e-9)
+    assert list(a[0]) == [0.5, -0.5]
+    f0 = a[0, 0] + a[0, 1] * k + b[0]
+    assert f0 < 1.0  # the margin is not reached with a binding box
+
+
+def _svm_data(seed, n, dim, C):
+    rng = np.random.default_rng(seed)
+    protos = rng.uniform(0.5, 1.5, (C, dim))
+    lab = rng.integers(0, C, n).astype(np.int32)
+    X = rng.poisson(3.0 * protos[lab]).astype(np.float64)
+    X /= np.maximum(X.sum(1, keepdims=True), 1.0)
+    Xt = rng.poisson(3.0 * protos[rng.integers(0, C, 40)]).astype(np.float64)
+    Xt /= np.maximum(Xt.sum(1, keepdims=True), 1.0)
+    return X, lab, Xt
+
+
+def test_svm_train_matches_libsvm_and_kkt(orc):
+    """One-vs-rest training against scikit-learn's SVC (libsvm: the same dual, the same working
+    set rule) on decision values, and the KKT conditions at the solution."""
+    sk = pytest.importorskip("sklearn.svm")
+    X, lab, Xt = _svm_data(3, 90, 40, 3)
+    gamma, cost, eps = 5.0, 2.0, 1e-6
+    a, b, it = orc.svm_train_rbf(X, lab, 3, gamma, cost, eps=eps)
+    K = lambda A, B: np.exp(-gamma * ((A[:, None, :] - B[None, :, :]) ** 2).sum(-1))
+    f = K(Xt, X) @ a.T + b
+    ftr = K(X, X) @ a.T + b
+    for c in range(3):
+        y = np.where(lab == c, 1, -1)
+        m = sk.SVC(kernel="rbf", gamma=gamma, C=cost, tol=eps).fit(X, y)
+        assert np.abs(m.decision_function(Xt) - f[:, c]).max() < 1e-5
+        alpha = a[c] * y
+        assert (alpha >= 0).all() and (alpha <= cost).all() and abs((y * alpha).sum()) < 1e-9
+        yf = y * ftr[:, c]
+        free = (alpha > 1e-9) & (alpha < cost - 1e-9)
+        assert (yf[alpha <= 1e-9] >= 1 - 1e-4).all()
+        assert (yf[alpha >= cost - 1e-9] <= 1 + 1e-4).all()
+        assert np.abs(yf[free] - 1).max() < 1e-4
+    # a class with no member: every alpha stays 0 and f = b = -1 (all rows are "rest")
+    a2, b2, it2 = orc.svm_train_rbf(X, lab, 4, gamma, cost, eps=eps)
+    assert (a2[3] == 0).all() and b2[3] == -1.0 and it2[3] == 0
