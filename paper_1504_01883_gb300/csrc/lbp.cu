@@ -7,11 +7,11 @@
 //
 // The fused kernel is persistent: one CTA per half-SM slot walks over faces.  Per face:
 //   P1  every thread resamples 8 groups of 4 crop pixels (grey bilinear, depth nearest);
-//       grey goes to shared memory, the 32 depth values stay in registers, and the
-//       high byte of each depth feeds a 256-bin histogram (warp-aggregated when a
-//       warp's values span at most two bins, as on a smooth face).
-//   P2/P3  radix select of the lower median: the high-byte bin holding rank (n-1)/2,
-//       then a low-byte histogram restricted to that bin.
+//       grey goes to shared memory, the 32 depth values stay in registers and are counted
+//       into a coarse histogram of 1024 mm bins (eight 8-bit counters per thread in one
+//       64-bit word, summed over the warp with redux).
+//   P2/P3  radix select of the lower median: the coarse bin holding rank (n-1)/2, then a
+//       1 mm histogram restricted to that bin.
 //   P4  mask bytes (0x80 = valid) from the registers.
 //   P5  one thread per half cell (4 x 8 pixels) walks down its 8 rows with a
 //       3-row sliding window of packed words and computes four codes per step
@@ -92,8 +92,8 @@ struct __align__(16) Smem {
     uint32_t hist[Cfg<S>::HW * Cfg<S>::NT];  // thread-private 8-bit counts, word (bin/4)*NT + t
     uint2 colmap[S];                   // taps per crop column, read two at a time (uint4)
     uint2 rowmap[S];                   // taps per crop row
-    uint32_t h1[256];                  // depth high-byte histogram
-    uint32_t h2[256];                  // depth low-byte histogram inside the median's bin
+    uint32_t h1[64];                   // coarse depth histogram: bins of 1024 mm (d >> 10)
+    uint32_t h2[1024];                 // fine histogram (d & 1023) inside the median's coarse bin
     uint32_t cnt[Cfg<S>::NT];          // valid centres per half cell
     float nvf[Cfg<S>::G * Cfg<S>::G];  // valid centres per cell (as float) ...
     float rcp[Cfg<S>::G * Cfg<S>::G];  // ... and its IEEE reciprocal (0 for an empty cell)
@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             gsrc += (size_t)face * S * S;
             dsrc += (size_t)face * S * S;
         }
-        for (int i = tid; i < 256; i += NT) {
-            sm.h1[i] = 0;
+        for (int i = tid; i < 1024; i += NT) {
+            if (i < 64) sm.h1[i] = 0;
             sm.h2[i] = 0;
         }
 #pragma unroll
@@ -240,49 +240,46 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             dreg[2 * k] = d01;
             dreg[2 * k + 1] = d23;
         }
+        {
+            // coarse histogram of the non-zero depths (bins of 1024 mm): a thread holds 32 depths,
+            // so eight 8-bit counters in one 64-bit word count keys 0..7 (depths below 8192 mm);
+            // the warp sums them as 16-bit fields (at most 1024 each) and lane 0 adds them to the
+            // histogram.  Rarer depths of 8192 mm and beyond count with atomics.
+            unsigned long long cnt8 = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            // high-byte histogram of the non-zero depths.  The warp's two lowest bins (the face,
-            // which is nearer than the background) are counted with warp reductions and one
-            // atomic each; only the other values (background, spread over many bins) use
-            // per-value atomics, so no bin sees many same-address atomics in one instruction.
-            const uint32_t d01 = dreg[2 * k], d23 = dreg[2 * k + 1];
-            const uint32_t dv4[4] = {d01 & 0xFFFFu, d01 >> 16, d23 & 0xFFFFu, d23 >> 16};
-            int kmin = 256;
+            for (int i = 0; i < 16; ++i) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (dv4[e]) kmin = min(kmin, (int)(dv4[e] >> 8));
-            const int wmin = __reduce_min_sync(FULL, kmin);
-            if (wmin < 256) {
-                unsigned clo = 0, chi = 0;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (dv4[e]) {
-                        const int key = (int)(dv4[e] >> 8);
-                        if (key == wmin)
-                            ++clo;
-                        else if (key == wmin + 1)
-                            ++chi;
-                        else
-                            atomicAdd(&sm.h1[key], 1u);
-                    }
+                for (int hh = 0; hh < 2; ++hh) {
+                    const uint32_t d = (dreg[i] >> (16 * hh)) & 0xFFFFu;
+                    const uint32_t key = d >> 10;
+                    if (key < 8)
+                        cnt8 += (d ? 1ull : 0ull) << (8 * key);
+                    else
+                        atomicAdd(&sm.h1[key], 1u);
                 }
-                const unsigned tlo = __reduce_add_sync(FULL, clo);
-                const unsigned thi = __reduce_add_sync(FULL, chi);
-                if (lane == 0) {
-                    atomicAdd(&sm.h1[wmin], tlo);
-                    if (thi) atomicAdd(&sm.h1[wmin + 1], thi);
-                }
+            }
+            const unsigned long long ev = cnt8 & 0x00FF00FF00FF00FFull;          // keys 0, 2, 4, 6
+            const unsigned long long od = (cnt8 >> 8) & 0x00FF00FF00FF00FFull;   // keys 1, 3, 5, 7
+            const uint32_t s02 = __reduce_add_sync(FULL, (uint32_t)ev);
+            const uint32_t s46 = __reduce_add_sync(FULL, (uint32_t)(ev >> 32));
+            const uint32_t s13 = __reduce_add_sync(FULL, (uint32_t)od);
+            const uint32_t s57 = __reduce_add_sync(FULL, (uint32_t)(od >> 32));
+            if (lane == 0) {
+                const uint32_t c8[8] = {s02 & 0xFFFFu, s13 & 0xFFFFu, s02 >> 16, s13 >> 16,
+                                        s46 & 0xFFFFu, s57 & 0xFFFFu, s46 >> 16, s57 >> 16};
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (c8[k]) atomicAdd(&sm.h1[k], c8[k]);
             }
         }
         __syncthreads();
 
-        // ---- P2: high-byte bin of the lower median (rank (n-1)/2 of the non-zero depths) ---
+        // ---- P2: coarse bin of the lower median (rank (n-1)/2 of the non-zero depths) -----
         if (warp == 0) {
-            uint32_t s8[8], lsum = 0;
+            uint32_t s8[2], lsum = 0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                s8[j] = sm.h1[lane * 8 + j];
+            for (int j = 0; j < 2; ++j) {
+                s8[j] = sm.h1[lane * 2 + j];
                 lsum += s8[j];
             }
             uint32_t incl = lsum;
@@ -301,9 +298,9 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 if (lane == src) {
                     uint32_t c = excl;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+                    for (int j = 0; j < 2; ++j) {
                         if (b1 < 0 && k < c + s8[j]) {
-                            b1 = lane * 8 + j;
+                            b1 = lane * 2 + j;
                             k1 = (int)(k - c);
                         }
                         c += s8[j];
@@ -320,24 +317,21 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         __syncthreads();
         const int b1 = sm.info[0];
 
-        // ---- P3: low byte of the median inside bin b1 ------------------------------------
+        // ---- P3: the median's value inside coarse bin b1 (1 mm bins) ----------------------
         int med = -1;
         if (b1 >= 0) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const uint32_t lo = dreg[i] & 0xFFFFu, hi = dreg[i] >> 16;
-                if (lo && (int)(lo >> 8) == b1) atomicAdd(&sm.h2[lo & 255u], 1u);
-                if (hi && (int)(hi >> 8) == b1) atomicAdd(&sm.h2[hi & 255u], 1u);
+                if (lo && (int)(lo >> 10) == b1) atomicAdd(&sm.h2[lo & 1023u], 1u);
+                if (hi && (int)(hi >> 10) == b1) atomicAdd(&sm.h2[hi & 1023u], 1u);
             }
             __syncthreads();
             if (warp == 0) {
                 const uint32_t k1 = (uint32_t)sm.info[1];
-                uint32_t s8[8], lsum = 0;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    s8[j] = sm.h2[lane * 8 + j];
-                    lsum += s8[j];
-                }
+                uint32_t lsum = 0;  // 32 fine bins per lane, read twice from shared memory
+#pragma unroll 8
+                for (int j = 0; j < 32; ++j) lsum += sm.h2[lane * 32 + j];
                 uint32_t incl = lsum;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
@@ -350,14 +344,14 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 int b2 = -1;
                 if (lane == src) {
                     uint32_t c = excl;
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        if (b2 < 0 && k1 < c + s8[j]) b2 = lane * 8 + j;
-                        c += s8[j];
+                    for (int j = 0; j < 32; ++j) {
+                        const uint32_t hj = sm.h2[lane * 32 + j];
+                        if (b2 < 0 && k1 < c + hj) b2 = lane * 32 + j;
+                        c += hj;
                     }
                 }
                 b2 = __shfl_sync(FULL, b2, src);
-                if (lane == 0) sm.info[2] = b1 * 256 + b2;
+                if (lane == 0) sm.info[2] = b1 * 1024 + b2;
             }
             __syncthreads();
             med = sm.info[2];
