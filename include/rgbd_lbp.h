@@ -393,6 +393,13 @@ int svm_score_noalloc(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const
  *   Asynchronous on stream.  Errors: RGBD_ERR_ARG for n < 0 or NULL pointers with n > 0. */
 int rgbd_debug_expm1(const float* z, float* out, int n, void* stream);
 
+/* rgbd_debug_wait_timeout -- runs, for a test of the failure path, the bounded barrier wait of
+ * the tensor-core kernel on a phase that nothing completes: after limit_ns (1 us .. 100 ms) the
+ * wait gives up, sets RGBD_STATUS_WAIT_TIMEOUT in the context status and the kernel returns, so
+ * the context stays usable.  *result (device int) receives 1 when the wait gave up.
+ * Errors: RGBD_ERR_ARG. */
+int rgbd_debug_wait_timeout(rgbd_ctx* ctx, uint64_t limit_ns, int* result, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,7 @@ def lib():
             "rgbd_ctx_set_tuning": [P, I, I],
             "rgbd_track_nearest": [P, P, I, P, I, P, P],
             "rgbd_debug_expm1": [P, P, I, P],
+            "rgbd_debug_wait_timeout": [P, ctypes.c_uint64, P, P],
             "rgbd_face_roi": [P, P, I, I, I, P, P, I, P, P],
             "svm_train_rbf": [P, P, P, I, I, P, I, F, F, F, I, P, P, P, P],
             "rgbd_track_streams": [P, P, P, P, I, I, I, P, P, P, I, P, P, P],
@@ -296,6 +297,14 @@ def rgbd_track_streams(ctx, state, frame_stream, frame_start, rects, labels, ids
                                     _p(rects) if n else None, n, _p(labels) if n else None, _p(ids) if n else None,
                                     _stream(stream)))
     return ids
+
+
+def rgbd_debug_wait_timeout(ctx, limit_ns, stream=None):
+    """Runs the scoring kernel's bounded wait on a barrier nothing completes; returns the device
+    result (1 = the wait gave up after limit_ns and flagged RGBD_STATUS_WAIT_TIMEOUT)."""
+    res = torch.full((1,), -1, dtype=torch.int32, device=torch.device("cuda", ctx.device))
+    _check(lib().rgbd_debug_wait_timeout(ctx.handle, int(limit_ns), _p(res), _stream(stream)))
+    return res
 
 
 def rgbd_debug_expm1(z, stream=None):

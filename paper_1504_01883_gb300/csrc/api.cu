@@ -158,6 +158,7 @@ int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value) {
 int rgbd_crop_affine(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, int n_frames, int H,
                      int W, const rgbd_rect* rects, const int32_t* affine_q16, int n_rects,
                      int out_h, int out_w, uint8_t* out_grey, uint16_t* out_depth, void* stream) {
+    rgbd::NvtxRange nvtx_range("rgbd_crop_affine");
     CHECK_ARG(ctx != nullptr, "rgbd_crop_affine: ctx is NULL");
     CHECK_ARG(n_rects >= 0, "rgbd_crop_affine: n_rects %d < 0", n_rects);
     if (n_rects == 0) return RGBD_OK;
@@ -190,6 +191,7 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
                        int H, int W, const rgbd_rect* rects, const int32_t* affine_q16, int n,
                        int crop, int cell, int mask_mm, int flags, uint16_t* feats, int x_dtype,
                        void* x_out, int k_pad, float x_scale, float* xsq_out, void* stream) {
+    rgbd::NvtxRange nvtx_range("lbp_fused_features");
     CHECK_ARG(ctx != nullptr, "lbp_fused_features: ctx is NULL");
     CHECK_ARG(n >= 0, "lbp_fused_features: n %d < 0", n);
     CHECK_ARG((flags & ~(RGBD_LBP_GE | RGBD_LBP_NBR_IGNORE_MASK | RGBD_LBP_FACE_HIST256)) == 0,
@@ -249,6 +251,7 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
 int lbp_normalize_features(rgbd_ctx* ctx, const uint16_t* feats, int n, int dim, int nbins,
                            int x_dtype, void* x_out, int k_pad, float x_scale, float* xsq_out,
                            void* stream) {
+    rgbd::NvtxRange nvtx_range("lbp_normalize_features");
     CHECK_ARG(ctx != nullptr, "lbp_normalize_features: ctx is NULL");
     CHECK_ARG(n >= 0 && dim > 0 && nbins > 0 && dim % nbins == 0,
               "lbp_normalize_features: n %d dim %d nbins %d", n, dim, nbins);
@@ -265,6 +268,7 @@ int lbp_normalize_features(rgbd_ctx* ctx, const uint16_t* feats, int n, int dim,
 
 int svm_score(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* xsq, int n,
               float x_scale, float* scores, int32_t* labels, void* stream) {
+    rgbd::NvtxRange nvtx_range("svm_score");
     CHECK_ARG(ctx != nullptr && model != nullptr, "svm_score: ctx or model is NULL");
     CHECK_ARG(model->scorable, "svm_score: model was packed without coefficients");
     CHECK_ARG(n >= 0, "svm_score: n %d < 0", n);

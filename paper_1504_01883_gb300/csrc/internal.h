@@ -6,8 +6,18 @@
 #include <stdint.h>
 
 #include "rgbd_lbp.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace rgbd {
+
+// NVTX range over one C-ABI call (a no-op unless a profiler is attached): names each stage in
+// nsys / ncu timelines.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kBins = 59;     // uniform-pattern bins per cell (58 uniform + 1)
 constexpr int kCell = 8;      // cell side in pixels

@@ -42,6 +42,7 @@ int scratch_address(int device, void** out) {
 
 extern "C" int svm_score_noalloc(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* xsq, int n,
                                  float x_scale, float* scores, int32_t* labels, void* stream) {
+    rgbd::NvtxRange nvtx_range("svm_score_noalloc");
     using namespace rgbd;
     if (!ctx || !model) return set_error(RGBD_ERR_ARG, "svm_score_noalloc: ctx or model is NULL");
     if (!model->scorable) return set_error(RGBD_ERR_ARG, "svm_score_noalloc: model was packed without coefficients");

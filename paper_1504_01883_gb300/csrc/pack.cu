@@ -130,6 +130,7 @@ extern "C" {
 int svm_train_data_pack(rgbd_ctx* ctx, const uint16_t* sv_feats, int n_sv, int dim, int nbins,
                         const float* coef, const float* bias, int n_classes, int kernel, float gamma,
                         int dtype, rgbd_svm** model_out, void* stream) {
+    rgbd::NvtxRange nvtx_range("svm_train_data_pack");
     if (!ctx || !model_out) return set_error(RGBD_ERR_ARG, "svm_train_data_pack: ctx or model_out is NULL");
     *model_out = nullptr;
     if (kernel != RGBD_KERNEL_LINEAR && kernel != RGBD_KERNEL_RBF)

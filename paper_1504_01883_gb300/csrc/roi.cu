@@ -120,6 +120,7 @@ using namespace rgbd;
 
 extern "C" int rgbd_face_roi(rgbd_ctx* ctx, const uint16_t* depth, int n_frames, int H, int W, const rgbd_calib* calib,
                              const rgbd_rect* colour_rects, int n, rgbd_rect* depth_rects, void* stream) {
+    rgbd::NvtxRange nvtx_range("rgbd_face_roi");
     if (!ctx) return set_error(RGBD_ERR_ARG, "rgbd_face_roi: ctx is NULL");
     if (!calib) return set_error(RGBD_ERR_ARG, "rgbd_face_roi: calib is NULL");
     if (n < 0 || n_frames <= 0 || H <= 0 || W <= 0)

@@ -174,13 +174,14 @@ __device__ __forceinline__ bool bar_test(uint32_t a, uint32_t parity) {
 // The deadline clock (%globaltimer, slow to read) is consulted only after a failed test and then
 // once every 16 further tests, so that it never sits on the critical path of a k-block handshake.
 template <bool CL = false>
-__device__ __noinline__ bool bar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+__device__ __noinline__ bool bar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, uint32_t* status,
+                                      uint64_t limit_ns = WAIT_NS) {
     if (bar_try<CL>(a, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (bar_try<CL>(a, parity)) return true;
         if (*abort_flag) return false;
-        if ((it & 15u) == 0 && globaltimer() - t0 > WAIT_NS) {
+        if ((it & 15u) == 0 && globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(status, RGBD_STATUS_WAIT_TIMEOUT);
             return false;
@@ -1001,6 +1002,19 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
                                 m->bias, m->gamma, scores, labels, s);
 }
 
+// The bounded wait of the scoring kernel on a barrier phase that nothing completes: after
+// `limit_ns` it flags RGBD_STATUS_WAIT_TIMEOUT and returns (the path every stalled wait takes).
+__global__ void wait_probe_kernel(uint32_t* status, uint64_t limit_ns, int* waited_out) {
+    __shared__ __align__(8) uint64_t barrier;
+    __shared__ int abort_flag;
+    const uint32_t b = smem_u32(&barrier);
+    bar_init(b, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const bool ok = bar_wait<false>(b, 0, &abort_flag, status, limit_ns);
+    *waited_out = ok ? 0 : (abort_flag ? 1 : 2);
+}
+
 __global__ void expm1_probe_kernel(const float* __restrict__ z, float* __restrict__ out, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         out[i] = expm1_near0(z[i]);
@@ -1040,4 +1054,16 @@ extern "C" int rgbd_debug_expm1(const float* z, float* out, int n, void* stream)
     expm1_probe_kernel<<<std::min((n + 255) / 256, 1024), 256, 0, (cudaStream_t)stream>>>(z, out, n);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? RGBD_OK : cuda_error(e, "rgbd_debug_expm1");
+}
+
+extern "C" int rgbd_debug_wait_timeout(rgbd_ctx* ctx, uint64_t limit_ns, int* result, void* stream) {
+    using namespace rgbd;
+    if (!ctx || !result) return set_error(RGBD_ERR_ARG, "rgbd_debug_wait_timeout: NULL pointer");
+    if (limit_ns < 1000 || limit_ns > 100000000ull)
+        return set_error(RGBD_ERR_ARG, "rgbd_debug_wait_timeout: limit %llu ns (1 us .. 100 ms)",
+                         (unsigned long long)limit_ns);
+    DeviceGuard g(ctx->props.device);
+    wait_probe_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctx->d_status, limit_ns, result);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RGBD_OK : cuda_error(e, "rgbd_debug_wait_timeout");
 }

@@ -125,6 +125,7 @@ extern "C" int rgbd_track_streams(rgbd_ctx* ctx, rgbd_rect* state_rects, int32_t
                                   int n_streams, int max_faces, int n_frames, const int32_t* frame_stream,
                                   const int32_t* frame_start, const rgbd_rect* rects, int n, const int32_t* labels,
                                   int32_t* ids, void* stream) {
+    rgbd::NvtxRange nvtx_range("rgbd_track_streams");
     if (!ctx) return set_error(RGBD_ERR_ARG, "rgbd_track_streams: ctx is NULL");
     if (n_streams < 1 || max_faces < 1 || max_faces > kTrackMaxFaces || n_frames < 0 || n < 0)
         return set_error(RGBD_ERR_ARG, "rgbd_track_streams: n_streams %d, max_faces %d (1..%d), n_frames %d, n %d",
@@ -144,6 +145,7 @@ extern "C" int rgbd_track_streams(rgbd_ctx* ctx, rgbd_rect* state_rects, int32_t
 
 extern "C" int rgbd_track_nearest(rgbd_ctx* ctx, const rgbd_rect* prev, int n_prev, const rgbd_rect* cur, int n_cur,
                                   int32_t* match, void* stream) {
+    rgbd::NvtxRange nvtx_range("rgbd_track_nearest");
     if (!ctx) return set_error(RGBD_ERR_ARG, "rgbd_track_nearest: ctx is NULL");
     if (n_prev < 0 || n_cur < 0) return set_error(RGBD_ERR_ARG, "rgbd_track_nearest: negative count");
     if (n_prev == 0) return RGBD_OK;

@@ -205,6 +205,7 @@ using namespace rgbd;
 extern "C" int svm_train_rbf(rgbd_ctx* ctx, const float* x, const float* xsq, int n, int k_pad, const int32_t* labels,
                              int n_classes, float gamma, float cost, float eps, int max_iter, float* coef, float* bias,
                              int32_t* iters, void* stream) {
+    rgbd::NvtxRange nvtx_range("svm_train_rbf");
     if (!ctx) return set_error(RGBD_ERR_ARG, "svm_train_rbf: ctx is NULL");
     if (n < 2 || n > 16384 || k_pad <= 0 || n_classes < 1 || !(gamma > 0.f) || !(cost > 0.f) || !(eps > 0.f) ||
         max_iter < 0 || max_iter > 2000000)

@@ -247,6 +247,25 @@ def test_epilogue_expm1_accuracy(B):
     assert np.max(np.abs(ours - cuda) / ulp) <= 3.0
 
 
+def test_bounded_wait_gives_up_and_context_survives(B, ctx, orc):
+    """Failure path of the tensor-core kernel's waits: a barrier phase that nothing completes makes
+    the bounded wait give up after its limit (2 ms here), flag RGBD_STATUS_WAIT_TIMEOUT and return
+    instead of hanging; the same context then scores correctly."""
+    ctx.status(clear=True)
+    res = B.rgbd_debug_wait_timeout(ctx, 2_000_000)
+    torch.cuda.synchronize()
+    assert res.item() == 1
+    assert ctx.status(clear=True) & B.STATUS_WAIT_TIMEOUT
+    X, SV, a, b, gamma = _scoring_problem(9, 20, 300, 10)
+    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype="bf16")
+    x, q = B.lbp_normalize_features(ctx, dev_u16(X), "bf16")
+    s, _ = B.svm_score(ctx, model, x, q)
+    assert ctx.status() == 0
+    x64, sv64 = orc.normalize_f64(X), orc.normalize_f64(SV)
+    ref = orc.svm_rbf(x64, sv64, a, b, gamma)
+    assert rel_score_error(s.cpu().numpy(), ref, rbf_error_scale(x64, sv64, a, b, gamma)) <= 5e-5
+
+
 @pytest.mark.parametrize("mc", [3, 1, 2])
 @pytest.mark.parametrize("dt", ["bf16", "fp8", "tf32", "bf16x3"])
 def test_tensor_core_pairing_modes(B, ctx, orc, dt, mc):
