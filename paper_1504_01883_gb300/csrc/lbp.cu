@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
 
     const bool strict = !(a.flags & RGBD_LBP_GE);
     const bool nbr_ignore = (a.flags & RGBD_LBP_NBR_IGNORE_MASK) != 0;
+    const bool masked_grey = strict && !nbr_ignore;  // the default rule (readings c2, c7)
     const int x_dtype = a.x_out ? a.x_dtype : 0;
 
     for (int face = blockIdx.x; face < a.n; face += gridDim.x) {
@@ -371,6 +372,9 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     m |= valid ? (0x80u << (8 * e)) : 0u;
                 }
                 mw[tid + k * NT] = m;
+                // strict compares with masked neighbours: a grey of 0 never compares greater, so
+                // zeroing the invalid pixels once replaces the per-neighbour masks of P5
+                if (masked_grey) sm.img[tid + k * NT] &= (m >> 7) * 0xFFu;
             }
         }
         __syncthreads();
@@ -398,13 +402,36 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 R = __byte_perm(c0, r1, 0x4321);
             };
             uint32_t gUL, gUC, gUR, gCL, gCC, gCR, gDL, gDC, gDR;
+            uint32_t nvalid = 0;
+            uint8_t* hb_t = reinterpret_cast<uint8_t*>(sm.hist) + 4 * tid;  // this thread's counters
+            if (masked_grey) {
+                // invalid pixels read as grey 0 (P4): no neighbour masks, only the centre's
+                row3(GW, r0 - 1, gUL, gUC, gUR);
+                row3(GW, r0, gCL, gCC, gCR);
+#pragma unroll 2
+                for (int i = 0; i < 8; ++i) {
+                    row3(GW, r0 + i + 1, gDL, gDC, gDR);
+                    const uint32_t mC = MW[(r0 + i) * SW + wc];
+                    const uint32_t cb = (gCC & 0x7F7F7F7Fu) + 0x01010101u;
+                    const uint32_t code = (cmp_msb(gUL, gCC, cb) >> 7) | (cmp_msb(gUC, gCC, cb) >> 6) |
+                                          (cmp_msb(gUR, gCC, cb) >> 5) | (cmp_msb(gCR, gCC, cb) >> 4) |
+                                          (cmp_msb(gDR, gCC, cb) >> 3) | (cmp_msb(gDC, gCC, cb) >> 2) |
+                                          (cmp_msb(gDL, gCC, cb) >> 1) | cmp_msb(gCL, gCC, cb);
+                    nvalid += __popc(mC);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const uint32_t idx = ((mC >> (8 * e + 7)) & 1u) ? ((code >> (8 * e)) & 0xFFu) : 256u;
+                        hb_t[sm.lut[idx]] += 1;
+                    }
+                    gUL = gCL; gUC = gCC; gUR = gCR; gCL = gDL; gCC = gDC; gCR = gDR;
+                }
+                sm.cnt[tid] = nvalid;
+            } else {
             uint32_t mUL, mUC, mUR, mCL, mCC, mCR, mDL, mDC, mDR;
             row3(GW, r0 - 1, gUL, gUC, gUR);
             row3(MW, r0 - 1, mUL, mUC, mUR);
             row3(GW, r0, gCL, gCC, gCR);
             row3(MW, r0, mCL, mCC, mCR);
-            uint32_t nvalid = 0;
-            uint8_t* hb_t = reinterpret_cast<uint8_t*>(sm.hist) + 4 * tid;  // this thread's counters
 #pragma unroll 2
             for (int i = 0; i < 8; ++i) {
                 row3(GW, r0 + i + 1, gDL, gDC, gDR);
@@ -431,6 +458,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 mUL = mCL; mUC = mCC; mUR = mCR; mCL = mDL; mCC = mDC; mCR = mDR;
             }
             sm.cnt[tid] = nvalid;
+            }
         }
         __syncthreads();
 
