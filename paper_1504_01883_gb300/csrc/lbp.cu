@@ -98,6 +98,7 @@ struct __align__(16) Smem {
     float nvf[Cfg<S>::G * Cfg<S>::G];  // valid centres per cell (as float) ...
     float rcp[Cfg<S>::G * Cfg<S>::G];  // ... and its IEEE reciprocal (0 for an empty cell)
     float red[Cfg<S>::NT / 32];
+    uint32_t wsum[Cfg<S>::NT / 32];   // per-warp totals of the fine median histogram
     int info[4];
     uint16_t lut[257];                 // byte offset of each code's counter in a thread's histogram
                                        // (entry 256: the unused bin 59, where invalid centres go)
@@ -328,31 +329,36 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 if (hi && (int)(hi >> 10) == b1) atomicAdd(&sm.h2[hi & 1023u], 1u);
             }
             __syncthreads();
-            if (warp == 0) {
-                const uint32_t k1 = (uint32_t)sm.info[1];
-                uint32_t lsum = 0;  // 32 fine bins per lane, read twice from shared memory
-#pragma unroll 8
-                for (int j = 0; j < 32; ++j) lsum += sm.h2[lane * 32 + j];
-                uint32_t incl = lsum;
+            // rank k1 among the 1024 fine bins: every thread sums its 1024 / NT contiguous bins,
+            // the warps scan their threads, every thread adds the totals of the warps before its
+            // own, and the one thread whose bins hold rank k1 walks them
+            constexpr int BPT = (1024 + NT - 1) / NT;
+            const uint32_t k1 = (uint32_t)sm.info[1];
+            uint32_t lsum = 0;
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t t = __shfl_up_sync(FULL, incl, off);
-                    if (lane >= off) incl += t;
-                }
-                const uint32_t excl = incl - lsum;
-                const unsigned m = __ballot_sync(FULL, k1 >= excl && k1 < incl);
-                const int src = __ffs(m) - 1;
+            for (int j = 0; j < BPT; ++j)
+                if (tid * BPT + j < 1024) lsum += sm.h2[tid * BPT + j];
+            uint32_t incl = lsum;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, incl, off);
+                if (lane >= off) incl += t;
+            }
+            if (lane == 31) sm.wsum[warp] = incl;
+            __syncthreads();
+            uint32_t base = 0;
+            for (int w = 0; w < warp; ++w) base += sm.wsum[w];
+            const uint32_t excl = base + incl - lsum;
+            if (k1 >= excl && k1 < excl + lsum) {
+                uint32_t c = excl;
                 int b2 = -1;
-                if (lane == src) {
-                    uint32_t c = excl;
-                    for (int j = 0; j < 32; ++j) {
-                        const uint32_t hj = sm.h2[lane * 32 + j];
-                        if (b2 < 0 && k1 < c + hj) b2 = lane * 32 + j;
-                        c += hj;
-                    }
+#pragma unroll
+                for (int j = 0; j < BPT; ++j) {
+                    const uint32_t hj = tid * BPT + j < 1024 ? sm.h2[tid * BPT + j] : 0u;
+                    if (b2 < 0 && k1 < c + hj) b2 = tid * BPT + j;
+                    c += hj;
                 }
-                b2 = __shfl_sync(FULL, b2, src);
-                if (lane == 0) sm.info[2] = b1 * 1024 + b2;
+                sm.info[2] = b1 * 1024 + b2;
             }
             __syncthreads();
             med = sm.info[2];
