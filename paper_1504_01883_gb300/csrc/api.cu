@@ -257,9 +257,9 @@ int lbp_normalize_features(rgbd_ctx* ctx, const uint16_t* feats, int n, int dim,
               "lbp_normalize_features: n %d dim %d nbins %d", n, dim, nbins);
     CHECK_ARG(nbins <= 256, "lbp_normalize_features: nbins %d > 256", nbins);
     CHECK_ARG(x_dtype != 0, "lbp_normalize_features: x_dtype 0");
+    if (n == 0) return RGBD_OK;  // nothing to write: x_out may be NULL (an empty buffer)
     int rc = check_x_out("lbp_normalize_features", dim, x_dtype, x_out, k_pad, x_scale);
     if (rc) return rc;
-    if (n == 0) return RGBD_OK;
     CHECK_ARG(feats != nullptr, "lbp_normalize_features: feats is NULL");
     DeviceGuard g(ctx->props.device);
     return launch_normalize(feats, n, dim, nbins, x_dtype, x_out, k_pad, x_scale, xsq_out, nullptr,

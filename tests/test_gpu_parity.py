@@ -450,3 +450,65 @@ def test_svm_train_against_oracle_and_scoring(B, ctx, orc):
     srt = np.sort(f_orc, axis=1)
     clear = (srt[:, -1] - srt[:, -2]) > 5e-3
     assert (labels.cpu().numpy()[clear] == np.argmax(f_orc, axis=1)[clear]).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# The batch workload at full size, and empty inputs
+# ---------------------------------------------------------------------------------------------
+
+def test_full_batch_workload_sampled(B, ctx, orc):
+    """The headline batch at its full size (256 frames 640x480, 4096 faces of side 48-256, 4096
+    SVs x 64 classes, bf16 scoring) in the default launch layout: 32 sampled faces' features are
+    bit-exact and their scores within the bf16 bound of the fp64 oracle; labels agree wherever the
+    fp64 margin is clear of that bound."""
+    wl = synth.batching()
+    model = B.svm_train_data_pack(ctx, dev_u16(wl.sv_counts), dev_f32(wl.coef), dev_f32(wl.bias), gamma=wl.gamma,
+                                  dtype="bf16")
+    f, x, q = B.lbp_fused_features(ctx, dev_u8(wl.grey), dev_u16(wl.depth), B.rects_tensor(wl.rects), crop=128,
+                                   x_dtype="bf16")
+    s, lab = B.svm_score(ctx, model, x, q)
+    assert ctx.status() == 0
+    idx = np.linspace(0, wl.n_crops - 1, 32).astype(int)
+    want = orc.features_batch(wl.grey, wl.depth, wl.rects[idx], 128)
+    assert (host_u16(f)[idx] == want).all()
+    x64, sv64 = orc.normalize_f64(want), orc.normalize_f64(wl.sv_counts)
+    ref = orc.svm_rbf(x64, sv64, wl.coef, wl.bias, wl.gamma)
+    scale = rbf_error_scale(x64, sv64, wl.coef, wl.bias, wl.gamma)
+    assert rel_score_error(s.cpu().numpy()[idx], ref, scale) <= 5e-5
+    srt = np.sort(ref, axis=1)
+    clear = (srt[:, -1] - srt[:, -2]) > 2 * 5e-5 * scale.max()
+    assert (lab.cpu().numpy()[idx][clear] == orc.argmax(ref)[clear]).all()
+
+
+def test_empty_inputs(B, ctx, orc):
+    """Every batch entry point accepts zero items: nothing is launched, nothing is flagged."""
+    g, d, _ = synth.frames_with_rects(3, 1, 1, 48, 64, H=64, W=64)
+    gd, dd = dev_u8(g), dev_u16(d)
+    none = torch.zeros((0, 5), dtype=torch.int32, device="cuda")
+    og, od = B.rgbd_crop_affine(ctx, gd, dd, none, 32, 32)
+    assert og.shape == (0, 32, 32)
+    f, x, q = B.lbp_fused_features(ctx, gd, dd, none, crop=64, x_dtype="bf16")
+    assert f.shape[0] == 0 and x.shape[0] == 0
+    x0, q0 = B.lbp_normalize_features(ctx, torch.zeros((0, 3776), dtype=torch.int16, device="cuda"), "f32")
+    rng = synth.rng_for(4)
+    sv = synth.poisson_counts(rng, 300, 16 * 59)
+    a, b = synth.rbf_coefficients(rng, 10, 300)
+    for dt in ("f32", "bf16"):
+        model = B.svm_train_data_pack(ctx, dev_u16(sv), dev_f32(a), dev_f32(b), gamma=1.0 / (16 * 59), dtype=dt)
+        xe = torch.zeros(B.x_shape(B._dt(dt), 0, model.k_pad), dtype=B.x_torch_dtype(B._dt(dt)), device="cuda")
+        qe = torch.zeros((0,), dtype=torch.float32, device="cuda")
+        s, lab = B.svm_score(ctx, model, xe, qe)
+        assert s.shape == (0, 10)
+        if dt == "bf16":
+            s, lab = B.svm_score_noalloc(ctx, model, xe, qe)
+            assert s.shape == (0, 10)
+    assert B.rgbd_track_nearest(ctx, none, none).shape == (0,)
+    st = B.TrackState(2, 4)
+    ids = B.rgbd_track_streams(ctx, st, torch.zeros((0,), dtype=torch.int32, device="cuda"),
+                               torch.zeros((1,), dtype=torch.int32, device="cuda"), none,
+                               torch.zeros((0,), dtype=torch.int32, device="cuda"))
+    assert ids.shape == (0,)
+    cal = synth.calibration(rng, 64, 64)
+    assert B.rgbd_face_roi(ctx, dd, B.Calib.from_record(cal), none).shape == (0, 5)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
