@@ -88,12 +88,13 @@ int rgbd_ctx_create(int device, rgbd_ctx** out) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->props.smem_optin = (size_t)optin;
-    e = cudaMalloc(&c->d_status, sizeof(uint32_t));
+    e = cudaMalloc(&c->d_status, sizeof(uint32_t) * (1 + kFaceCounters));
     if (e != cudaSuccess) {
         delete c;
         return cuda_error(e, "rgbd_ctx_create: status word");
     }
-    e = cudaMemset(c->d_status, 0, sizeof(uint32_t));
+    c->d_counters = c->d_status + 1;
+    e = cudaMemset(c->d_status, 0, sizeof(uint32_t) * (1 + kFaceCounters));
     if (e != cudaSuccess) {
         cudaFree(c->d_status);
         delete c;
@@ -245,6 +246,7 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
     a.x_plane = (size_t)n * k_pad;
     a.xsq = xsq_out;
     a.status = ctx->d_status;
+    a.face_counter = ctx->d_counters + (ctx->counter_next++ % kFaceCounters);
     return launch_lbp_fused(ctx, a, (cudaStream_t)stream);
 }
 

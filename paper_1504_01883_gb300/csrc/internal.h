@@ -23,6 +23,7 @@ constexpr int kBins = 59;     // uniform-pattern bins per cell (58 uniform + 1)
 constexpr int kCell = 8;      // cell side in pixels
 constexpr int kKAlign = 128;  // k_pad granularity (elements)
 constexpr int kSvTile = 256;  // SVs per tensor-core tile; n_pad is a multiple of it
+constexpr int kFaceCounters = 256;  // face-queue counters per context (launches in flight at once)
 
 // Sets the thread's last error message (printf-style) and returns `code`.
 int set_error(int code, const char* fmt, ...);
@@ -42,7 +43,9 @@ struct rgbd_ctx {
     int tune_lbp_ctas_per_sm = 0;  // 0 = occupancy limit
     int tune_tc_splits = 0;        // 0 = cost model
     int tune_tc_multicast = 0;     // CTA pairing: 0 = auto, 1 = multicast, 2 = none, 3 = 2-CTA MMA
-    uint32_t* d_status = nullptr;  // device status word
+    uint32_t* d_status = nullptr;  // device status word, followed by kFaceCounters face-queue counters
+    uint32_t* d_counters = nullptr;
+    uint32_t counter_next = 0;     // next counter of the pool (a launch takes one and zeroes it)
     void* workspace = nullptr;
     size_t workspace_bytes = 0;
 };
@@ -117,6 +120,7 @@ struct LbpArgs {
     size_t x_plane;  // RGBD_DT_BF16X3: elements from the hi plane to the lo plane
     float* xsq;
     uint32_t* status;
+    uint32_t* face_counter;  // NULL: faces strided over CTAs; else a zeroed queue counter
 };
 int launch_lbp_fused(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s);
 

@@ -135,7 +135,9 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
     const bool masked_grey = strict && !nbr_ignore;  // the default rule (readings c2, c7)
     const int x_dtype = a.x_out ? a.x_dtype : 0;
 
-    for (int face = blockIdx.x; face < a.n; face += gridDim.x) {
+    // Faces: the first one by CTA index, then from the launch's queue counter (a CTA that
+    // finishes early takes the next face), or strided over the CTAs when there is no counter.
+    for (int face = blockIdx.x; face < a.n;) {
         __syncthreads();  // the previous face's output pass is done with shared memory
 
         // ---- P0: descriptor, tap maps, cleared histograms --------------------------------
@@ -581,6 +583,10 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 a.xsq[face] = t;
             }
         }
+        if (tid == 0)
+            sm.info[3] = a.face_counter ? (int)gridDim.x + (int)atomicAdd(a.face_counter, 1u) : face + (int)gridDim.x;
+        __syncthreads();
+        face = sm.info[3];
     }
 }
 
@@ -968,6 +974,10 @@ int launch_fused_t(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
     }
     const int per_sm = ctx->tune_lbp_ctas_per_sm > 0 ? std::min(ctx->tune_lbp_ctas_per_sm, blocks_per_sm) : blocks_per_sm;
     const int grid = (int)std::min<long long>((long long)a.n, (long long)per_sm * ctx->props.sm_count);
+    if (a.face_counter) {
+        cudaError_t e = cudaMemsetAsync(a.face_counter, 0, sizeof(uint32_t), s);
+        if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: face queue reset");
+    }
     lbp_fused_kernel<S><<<grid, Cfg<S>::NT, smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: launch");
