@@ -18,7 +18,8 @@
 //       with byte-SIMD compares; codes go through the uniform table into a
 //       thread-private 8-bit histogram (no atomics, no bank conflicts).
 //   P6/P7  half-cell histograms are summed into a uint16 staging row, which is
-//       written out coalesced together with the normalised row and its norm.
+//       written out coalesced together with the normalised row and its norm (bf16 rows
+//       read each quotient h / n from a per-CTA table of the 65 x 65 possible values).
 // Everything up to A4 is exact integer arithmetic.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -102,6 +103,8 @@ struct __align__(16) Smem {
     int info[4];
     uint16_t lut[257];                 // byte offset of each code's counter in a thread's histogram
                                        // (entry 256: the unused bin 59, where invalid centres go)
+    uint32_t qrow[Cfg<S>::G * Cfg<S>::G];  // 65 x valid centres of each cell: its row of qbf
+    uint16_t qbf[65 * 65];             // bf16 bits of the quotient h / n, entry 65 n + h (n, h <= 64)
 };
 
 template <int S>
@@ -128,6 +131,16 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             prefix += __popc(m);
         }
         if (lane == 0) sm.lut[256] = (uint16_t)(((59 >> 2) * NT) * 4 + (59 & 3));
+    }
+    // Quotient table of the bf16 output: a cell has at most 64 centres, so every normalised value
+    // is one of the 65 x 65 quotients h / n, computed once per CTA exactly as the other output
+    // types compute them (IEEE single quotient, then round to nearest even bf16).
+    for (int i = tid; i < 65 * 65; i += NT) {
+        const int n = i / 65, hh = i - n * 65;
+        const float n_f = (float)n, r_f = n ? __frcp_rn(n_f) : 0.f, h_f = (float)hh;
+        const float q0 = __fmul_rn(h_f, r_f);
+        const float rem = __fmaf_rn(-q0, n_f, h_f);
+        sm.qbf[i] = __bfloat16_as_ushort(__float2bfloat16_rn(__fmaf_rn(rem, r_f, q0)));
     }
 
     const bool strict = !(a.flags & RGBD_LBP_GE);
@@ -478,6 +491,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 const uint32_t nv = sm.cnt[2 * c] + sm.cnt[2 * c + 1];
                 sm.nvf[c] = (float)nv;
                 sm.rcp[c] = nv ? __frcp_rn((float)nv) : 0.f;
+                sm.qrow[c] = nv * 65;
             }
             const int w0 = h ? 8 : 0, w1 = h ? C::HW : 8;
             for (int w = w0; w < w1; ++w) {
@@ -501,7 +515,25 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 hv = *reinterpret_cast<const uint2*>(stg + j);
                 if (a.feats) *reinterpret_cast<uint2*>(a.feats + (size_t)face * DIM + j) = hv;
             }
-            if (x_dtype) {
+            if (x_dtype == RGBD_DT_BF16) {
+                // bf16 rows: one table read per value
+                uint32_t pk[2] = {0u, 0u};
+                if (j < DIM) {
+                    const int c0 = j / kBins;
+                    const int split = (c0 + 1) * kBins;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int cc = (j + e < split) ? c0 : c0 + 1;
+                        const uint32_t hh = ((e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0xFFFFu;
+                        const uint32_t qb = sm.qbf[sm.qrow[cc] + hh];
+                        const float f = __uint_as_float(qb << 16);
+                        sq = fmaf(f, f, sq);
+                        pk[e >> 1] |= qb << (16 * (e & 1));
+                    }
+                }
+                *reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(a.x_out) + (size_t)face * a.k_pad + j) =
+                    make_uint2(pk[0], pk[1]);
+            } else if (x_dtype) {
                 // x = h / n as the IEEE single quotient: q0 = h * (1/n), then one fma correction.
                 // For 0 <= h <= n <= 64 (a cell has 64 pixels) this reproduces div.rn exactly
                 // (checked exhaustively); an empty cell has h = 0 and rcp = 0, giving 0.
@@ -519,21 +551,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                         x[e] = __fmaf_rn(rem, r_f, q0);
                     }
                 }
-                if (x_dtype == RGBD_DT_BF16) {
-                    uint32_t pk[2];
-#pragma unroll
-                    for (int e = 0; e < 4; e += 2) {
-                        const __nv_bfloat16 q0 = __float2bfloat16_rn(x[e]);
-                        const __nv_bfloat16 q1 = __float2bfloat16_rn(x[e + 1]);
-                        const float f0 = __bfloat162float(q0), f1 = __bfloat162float(q1);
-                        sq = fmaf(f0, f0, sq);
-                        sq = fmaf(f1, f1, sq);
-                        pk[e >> 1] = (uint32_t)__bfloat16_as_ushort(q0) |
-                                     ((uint32_t)__bfloat16_as_ushort(q1) << 16);
-                    }
-                    *reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(a.x_out) +
-                                              (size_t)face * a.k_pad + j) = make_uint2(pk[0], pk[1]);
-                } else if (x_dtype == RGBD_DT_BF16X3) {
+                if (x_dtype == RGBD_DT_BF16X3) {
                     // hi = bf16(x) into the first plane, lo = bf16(x - hi) into the second
                     uint32_t ph[2], pl[2];
 #pragma unroll

@@ -66,7 +66,7 @@ struct Lay {
     static_assert(STAGES <= MAX_STAGES, "barrier slots");
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
-constexpr int NUM_WARPS = 11;
+constexpr int NUM_WARPS = 19;  // producer, MMA issuer, coefficient producer, 16 epilogue warps
 constexpr int NUM_THREADS = NUM_WARPS * 32;
 // Tensor memory: G at column 0 (256 columns), D at 256 (C_pad <= 128 columns), the two F slots
 // (128 rows x 64 bf16, packed in pairs: 32 columns each) at 384 and 416 -- or, with the second
@@ -171,22 +171,37 @@ __device__ __forceinline__ bool bar_test(uint32_t a, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait.  Returns false when the CTA is aborting (deadline passed here or elsewhere).
-// The deadline clock (%globaltimer, slow to read) is consulted only after a failed test and then
-// once every 16 further tests, so that it never sits on the critical path of a k-block handshake.
-template <bool CL = false>
+// The abort flag and the deadline clock (%globaltimer, slow to read) are consulted only once
+// every 16 failed tests, so that neither sits on the critical path of a k-block handshake; the
+// deadline counts from the first consultation.
+// SPIN polls with test_wait instead of try_wait: a thread suspended in try_wait resumes late
+// after the phase completes, which costs the ring producer ~8 % of the scoring kernel's time.
+// (The ring producer spins inline first: see bar_spin.)
+template <bool CL = false, bool SPIN = false>
 __device__ __noinline__ bool bar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, uint32_t* status,
                                       uint64_t limit_ns = WAIT_NS) {
-    if (bar_try<CL>(a, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
-        if (bar_try<CL>(a, parity)) return true;
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (SPIN ? bar_test<CL>(a, parity) : bar_try<CL>(a, parity)) return true;
+        if ((it & 15u) != 15u) continue;
         if (*abort_flag) return false;
-        if ((it & 15u) == 0 && globaltimer() - t0 > limit_ns) {
+        const uint64_t now = globaltimer();
+        if (t0 == 0) {
+            t0 = now;
+        } else if (now - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(status, RGBD_STATUS_WAIT_TIMEOUT);
             return false;
         }
     }
+}
+// The ring producer's wait, on the critical path of every k-block: an inline test_wait spin
+// (a call into bar_wait per k-block costs ~8 % of the scoring kernel), then the bounded wait.
+template <bool CL>
+__device__ __forceinline__ bool bar_spin(uint32_t a, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+    for (int i = 0; i < 4096; ++i)
+        if (bar_test<CL>(a, parity)) return true;
+    return bar_wait<CL, true>(a, parity, abort_flag, status);
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
     asm volatile(
@@ -386,7 +401,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bar_init(bar(B_EMPTY + s), MC ? 2 : 1);  // both CTAs' MMAs read a multicast stage
         }
         bar_init(bar(B_GFULL), 1);
-        bar_init(bar(B_GEMPTY), PAIR ? 16 : 8);  // the epilogue warps (of both CTAs of a pair)
+        bar_init(bar(B_GEMPTY), PAIR ? 32 : 16);  // the epilogue warps (of both CTAs of a pair)
         for (int s = 0; s < 2; ++s) {
             // 4 epilogue warps (per CTA of a pair) + the coefficient producer
             bar_init(bar(B_FFULL + s), PAIR ? 8 + 1 : 4 + 1);
@@ -442,7 +457,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const int pass = kt / p.k_blocks, kb = kt - pass * p.k_blocks;
                     const CUtensorMap* mx = (pass == 2) ? &tm_x2 : &tm_x;
                     const CUtensorMap* msv = (pass == 1) ? &tm_sv2 : &tm_sv;
-                    if (!bar_wait<PAIR>(bar(B_EMPTY + stage), phase ^ 1u, abort_flag, p.status)) {
+                    if (!bar_spin<PAIR>(bar(B_EMPTY + stage), phase ^ 1u, abort_flag, p.status)) {
                         alive = false;
                         break;
                     }
@@ -644,9 +659,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
         }
     } else {
-        // ===================== epilogue: warps 3..10, one thread per row =====================
-        const int ew = warp - 3;           // 0..7
-        const int set = ew >> 2;           // chunks set, set + 2 of every tile
+        // ===================== epilogue: warps 3..18, one thread per row =====================
+        // Four sets of four warps; set s converts chunk s (columns 64 s .. 64 s + 63) of every
+        // tile.  A thread first reads its whole chunk of G, so that the issuer may start the
+        // next tile's G as soon as every set has read, and only then computes F.
+        const int ew = warp - 3;           // 0..15
+        const int set = ew >> 2;           // chunk of every tile
+        const int slot = set & 1;          // F slot and coefficient slot of the chunk (q & 1)
         const int quarter = warp & 3;      // TMEM lanes this warp may access
         const int row = quarter * 32 + lane;
         const int grow = m0 + row;
@@ -670,7 +689,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const uint32_t g_tmem = tmem + lane_addr;
             if (u == 0) {
                 // reference distance: mean d^2 over the valid columns of chunks 0 and 2 of the
-                // split's first tile; both warp sets compute the same value independently
+                // split's first tile; the four sets compute the same value independently
                 float sum = 0.f;
                 int cnt = 0;
 #pragma unroll 1
@@ -693,21 +712,30 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 }
                 r = sum / (float)max(cnt, 1);
             }
-#pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                const int c = set + 2 * h;  // chunk within the tile
+            {
+                const int c = set;          // chunk within the tile
                 const int q = 4 * u + c;    // chunk index within the split
                 uint32_t pk[32], pl[SPLIT2 ? 32 : 1];
+                uint32_t v[2][32];
+                TC_LD_X32(g_tmem + c * 64, v[0]);
+                TC_LD_X32(g_tmem + c * 64 + 32, v[1]);
+                tc_wait_ld();
+                // this set's only read of G for the tile
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    if (PAIR)
+                        bar_arrive_cluster(map_rank0(bar(B_GEMPTY)));
+                    else
+                        bar_arrive(bar(B_GEMPTY));
+                }
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
-                    uint32_t v[32];
-                    TC_LD_X32(g_tmem + c * 64 + half * 32, v);
-                    tc_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 32; j += 2) {
                         const int col = n0 + c * 64 + half * 32 + j;
-                        const float d0 = xs + __ldg(p.svsq + col) - 2.f * p.gscale * __uint_as_float(v[j]);
-                        const float d1 = xs + __ldg(p.svsq + col + 1) - 2.f * p.gscale * __uint_as_float(v[j + 1]);
+                        const float d0 = xs + __ldg(p.svsq + col) - 2.f * p.gscale * __uint_as_float(v[half][j]);
+                        const float d1 = xs + __ldg(p.svsq + col + 1) - 2.f * p.gscale * __uint_as_float(v[half][j + 1]);
                         const float f0 = expm1_near0(-p.gamma * (d0 - r)), f1 = expm1_near0(-p.gamma * (d1 - r));
                         const __nv_bfloat162 hv = __floats2bfloat162_rn(f0, f1);
                         pk[half * 16 + (j >> 1)] = *reinterpret_cast<const uint32_t*>(&hv);
@@ -717,33 +745,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         }
                     }
                 }
-                if (h == 1) {  // this set's last read of G for the tile
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) {
-                        if (PAIR)
-                            bar_arrive_cluster(map_rank0(bar(B_GEMPTY)));
-                        else
-                            bar_arrive(bar(B_GEMPTY));
-                    }
-                }
                 // the slot is free once the second MMA of chunk q - 2 is done
-                if (q >= 2 && !wait_warp(bar(B_FEMPTY + set), (uint32_t)(((q - 2) >> 1) & 1))) {
+                if (q >= 2 && !wait_warp(bar(B_FEMPTY + slot), (uint32_t)(((q - 2) >> 1) & 1))) {
                     alive = false;
                     break;
                 }
                 // F of this warp's 32 rows into the slot's 32 columns (row = TMEM lane); the lo
                 // part into the next 32 when the second product is split
-                TC_ST_X32(tmem + lane_addr + TMEM_F + F_SLOT * (uint32_t)set, pk);
-                if constexpr (SPLIT2) TC_ST_X32(tmem + lane_addr + TMEM_F + F_SLOT * (uint32_t)set + 32u, pl);
+                TC_ST_X32(tmem + lane_addr + TMEM_F + F_SLOT * (uint32_t)slot, pk);
+                if constexpr (SPLIT2) TC_ST_X32(tmem + lane_addr + TMEM_F + F_SLOT * (uint32_t)slot + 32u, pl);
                 tc_wait_st();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
                     if (PAIR)
-                        bar_arrive_cluster(map_rank0(bar(B_FFULL + set)));
+                        bar_arrive_cluster(map_rank0(bar(B_FFULL + slot)));
                     else
-                        bar_arrive(bar(B_FFULL + set));
+                        bar_arrive(bar(B_FFULL + slot));
                 }
             }
         }
