@@ -6,7 +6,9 @@
 //   A5 per-cell normalisation (and bf16 / FP8 quantisation) of the feature rows.
 //
 // The fused kernel is persistent: one CTA per half-SM slot walks over faces.  Per face:
-//   P1  every thread resamples 8 groups of 4 crop pixels (grey bilinear, depth nearest);
+//   P1  every thread resamples 8 groups of 4 crop pixels (grey bilinear, depth nearest;
+//       for rects at most 2 S wide the grey taps of two neighbouring pixels come from one
+//       aligned 8-byte window per source row, picked out with byte permutes);
 //       grey goes to shared memory, the 32 depth values stay in registers and are counted
 //       into a coarse histogram of 1024 mm bins (eight 8-bit counters per thread in one
 //       64-bit word, summed over the warp with redux).
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         // ---- P0: descriptor, tap maps, cleared histograms --------------------------------
         bool ok = true;
         rgbd_rect r = {0, 0, 0, S, S};
+        bool pair_win = false;  // grey taps read as 8-byte windows (rects at most 2 S wide)
         const uint8_t* gsrc = a.grey;
         const uint16_t* dsrc = a.depth;
         int64_t aff[6] = {0, 0, 0, 0, 0, 0};
@@ -166,6 +169,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             if (ok) {
                 gsrc += (size_t)r.frame * a.H * a.W;
                 dsrc += (size_t)r.frame * a.H * a.W;
+                pair_win = !a.affine && r.w <= 2 * S && (a.W & 3) == 0 && a.W >= 8 &&
+                           (reinterpret_cast<size_t>(a.grey) & 3) == 0;
             }
             if (ok && a.affine) {
 #pragma unroll
@@ -173,9 +178,22 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             } else if (ok) {
                 for (int i = tid; i < 2 * S; i += NT) {
                     if (i < S) {
+                        uint2 t = make_tap(rect_coord_q16(r.x, r.w, S, i), a.W);
+                        if (pair_win) {
+                            // grey taps of the column pair (4q + 2j, 4q + 2j + 1) inside one aligned
+                            // 8-byte window: .x = window start | o << 16 | (o + dx) << 20 | frac << 24.
+                            // The pair's first column is the previous lane (column threads form
+                            // whole warps: S is a multiple of 32).  With at most 2 S source columns
+                            // for S crop columns, neighbouring taps are at most 2 apart, so
+                            // o, o + dx <= 7 (the window start is clamped to W - 8).
+                            const uint32_t x_prev = __shfl_up_sync(FULL, t.x, 1);
+                            const uint32_t x_first = (i & 1) ? x_prev : t.x;
+                            const uint32_t wb = min((x_first & 0xFFFCu), (uint32_t)a.W - 8u);
+                            const uint32_t xa = t.x & 0xFFFFu, dx = (t.x >> 16) & 1u;
+                            t.x = wb | ((xa - wb) << 16) | ((xa + dx - wb) << 20) | (t.x & 0xFF000000u);
+                        }
                         // column u = 4q + e lives at uint2 index ((e / 2) * SW + q) * 2 + e % 2
-                        sm.colmap[(((i & 3) >> 1) * SW + (i >> 2)) * 2 + (i & 1)] =
-                            make_tap(rect_coord_q16(r.x, r.w, S, i), a.W);
+                        sm.colmap[(((i & 3) >> 1) * SW + (i >> 2)) * 2 + (i & 1)] = t;
                     } else {
                         const int v = i - S;
                         sm.rowmap[v] = make_tap(rect_coord_q16(r.y, r.h, S, v), a.H);
@@ -217,6 +235,30 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     const uint16_t* drow = dsrc + (size_t)rm.y * a.W;
                     const uint4* cm4 = reinterpret_cast<const uint4*>(sm.colmap);
                     uint32_t dv[4];
+                    if (pair_win) {
+#pragma unroll
+                    for (int e2 = 0; e2 < 2; ++e2) {
+                        const uint4 cc = cm4[e2 * SW + q];  // taps of columns 4q + 2 e2 and + 1
+                        const uint32_t wb = cc.x & 0xFFFFu;
+                        const uint32_t* wa = reinterpret_cast<const uint32_t*>(g0 + wb);
+                        const uint32_t* wv = reinterpret_cast<const uint32_t*>(g1 + wb);
+                        const uint32_t a0 = __ldg(wa), a1 = __ldg(wa + 1), b0 = __ldg(wv), b1 = __ldg(wv + 1);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const uint32_t cx = j ? cc.z : cc.x;
+                            const int fx = (int)(cx >> 24);
+                            const uint32_t pa = __byte_perm(a0, a1, cx >> 16), pb = __byte_perm(b0, b1, cx >> 16);
+                            const int p00 = (int)(pa & 0xFFu), p01 = (int)((pa >> 8) & 0xFFu);
+                            const int p10 = (int)(pb & 0xFFu), p11 = (int)((pb >> 8) & 0xFFu);
+                            const int h0 = (p00 << 8) + fx * (p01 - p00);
+                            const int h1 = (p10 << 8) + fx * (p11 - p10);
+                            const int acc = (h0 << 8) + (int)fy * (h1 - h0);
+                            const int e = 2 * e2 + j;
+                            gw |= (uint32_t)((acc + 32768) >> 16) << (8 * e);
+                            dv[e] = __ldg(drow + (j ? cc.w : cc.y));
+                        }
+                    }
+                    } else {
 #pragma unroll
                     for (int e2 = 0; e2 < 2; ++e2) {
                         const uint4 cc = cm4[e2 * SW + q];  // taps of columns 4q + 2 e2 and + 1
@@ -235,6 +277,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                             gw |= (uint32_t)((acc + 32768) >> 16) << (8 * e);
                             dv[e] = __ldg(drow + (j ? cc.w : cc.y));
                         }
+                    }
                     }
                     d01 = dv[0] | (dv[1] << 16);
                     d23 = dv[2] | (dv[3] << 16);
