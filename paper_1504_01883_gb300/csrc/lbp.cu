@@ -8,13 +8,14 @@
 // The fused kernel is persistent: one CTA per half-SM slot walks over faces.  Per face:
 //   P1  every thread resamples 8 groups of 4 crop pixels (grey bilinear, depth nearest;
 //       for rects at most 2 S wide the grey taps of two neighbouring pixels come from one
-//       aligned 8-byte window per source row, picked out with byte permutes);
-//       grey goes to shared memory, the 32 depth values stay in registers and are counted
-//       into a coarse histogram of 1024 mm bins (eight 8-bit counters per thread in one
-//       64-bit word, summed over the warp with redux).
+//       aligned 8-byte window per source row, and each horizontal interpolation is one byte
+//       permute and one 4-way byte dot product); grey and depth go to shared memory (the
+//       depths share their space with the P5 histograms) and the depths are counted into a
+//       coarse histogram of 1024 mm bins (eight 8-bit counters per thread in one 64-bit word,
+//       summed over the warp with redux).
 //   P2/P3  radix select of the lower median: the coarse bin holding rank (n-1)/2, then a
 //       1 mm histogram restricted to that bin.
-//   P4  mask bytes (0x80 = valid) from the registers.
+//   P4  mask bytes (0x80 = valid) from the depths.
 //   P5  one thread per half cell (4 x 8 pixels) walks down its 8 rows with a
 //       3-row sliding window of packed words and computes four codes per step
 //       with byte-SIMD compares; codes go through the uniform table into a
@@ -92,9 +93,13 @@ struct Cfg {
 template <int S>
 struct __align__(16) Smem {
     uint32_t img[2 * S * S / 4];       // grey words, then mask words; later the uint16 staging row
-    uint32_t hist[Cfg<S>::HW * Cfg<S>::NT];  // thread-private 8-bit counts, word (bin/4)*NT + t
+    union {
+        uint32_t hist[Cfg<S>::HW * Cfg<S>::NT];  // P5-P6: thread-private 8-bit counts, word (bin/4)*NT + t
+        uint32_t dep[S * S / 2];                 // P1-P4: the crop's depths, two per word, by item
+    };
     uint2 colmap[S];                   // taps per crop column, read two at a time (uint4)
     uint2 rowmap[S];                   // taps per crop row
+    uint16_t ncol[S];                  // nearest depth column per crop column (colmap order)
     uint32_t h1[64];                   // coarse depth histogram: bins of 1024 mm (d >> 10)
     uint32_t h2[1024];                 // fine histogram (d & 1023) inside the median's coarse bin
     uint32_t cnt[Cfg<S>::NT];          // valid centres per half cell
@@ -179,9 +184,12 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 for (int i = tid; i < 2 * S; i += NT) {
                     if (i < S) {
                         uint2 t = make_tap(rect_coord_q16(r.x, r.w, S, i), a.W);
+                        const int ci = (((i & 3) >> 1) * SW + (i >> 2)) * 2 + (i & 1);
                         if (pair_win) {
                             // grey taps of the column pair (4q + 2j, 4q + 2j + 1) inside one aligned
-                            // 8-byte window: .x = window start | o << 16 | (o + dx) << 20 | frac << 24.
+                            // 8-byte window starting at wb: .x = byte selector (o, o + dx, o) | wb << 16,
+                            // .y = byte weights (255 - fx, fx, 1, 0), so that one byte permute and one
+                            // 4-way byte dot product give 256 p(o) + fx (p(o + dx) - p(o)).
                             // The pair's first column is the previous lane (column threads form
                             // whole warps: S is a multiple of 32).  With at most 2 S source columns
                             // for S crop columns, neighbouring taps are at most 2 apart, so
@@ -189,11 +197,13 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                             const uint32_t x_prev = __shfl_up_sync(FULL, t.x, 1);
                             const uint32_t x_first = (i & 1) ? x_prev : t.x;
                             const uint32_t wb = min((x_first & 0xFFFCu), (uint32_t)a.W - 8u);
-                            const uint32_t xa = t.x & 0xFFFFu, dx = (t.x >> 16) & 1u;
-                            t.x = wb | ((xa - wb) << 16) | ((xa + dx - wb) << 20) | (t.x & 0xFF000000u);
+                            const uint32_t xa = t.x & 0xFFFFu, dx = (t.x >> 16) & 1u, fx = t.x >> 24;
+                            const uint32_t o = xa - wb, od = xa + dx - wb;
+                            sm.ncol[ci] = (uint16_t)t.y;
+                            t = make_uint2(o | (od << 4) | (o << 8) | (wb << 16), (255u - fx) | (fx << 8) | (1u << 16));
                         }
                         // column u = 4q + e lives at uint2 index ((e / 2) * SW + q) * 2 + e % 2
-                        sm.colmap[(((i & 3) >> 1) * SW + (i >> 2)) * 2 + (i & 1)] = t;
+                        sm.colmap[ci] = t;
                     } else {
                         const int v = i - S;
                         sm.rowmap[v] = make_tap(rect_coord_q16(r.y, r.h, S, v), a.H);
@@ -208,14 +218,12 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             if (i < 64) sm.h1[i] = 0;
             sm.h2[i] = 0;
         }
-#pragma unroll
-        for (int w = 0; w < C::HW; ++w) sm.hist[w * NT + tid] = 0;
         __syncthreads();
 
         // ---- P1: resample; grey to shared memory, depth to registers ----------------------
         // All taps are gathered first (independent loads, no warp-synchronous step in
         // between), then the high-byte histogram of the non-zero depths is built.
-        uint32_t dreg[16];
+        unsigned long long cnt8 = 0;  // coarse depth histogram, see below
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int item = tid + k * NT;  // = v * SW + q
@@ -239,23 +247,22 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
 #pragma unroll
                     for (int e2 = 0; e2 < 2; ++e2) {
                         const uint4 cc = cm4[e2 * SW + q];  // taps of columns 4q + 2 e2 and + 1
-                        const uint32_t wb = cc.x & 0xFFFFu;
+                        const uint32_t nn = reinterpret_cast<const uint32_t*>(sm.ncol)[e2 * SW + q];
+                        const uint32_t wb = cc.x >> 16;
                         const uint32_t* wa = reinterpret_cast<const uint32_t*>(g0 + wb);
                         const uint32_t* wv = reinterpret_cast<const uint32_t*>(g1 + wb);
                         const uint32_t a0 = __ldg(wa), a1 = __ldg(wa + 1), b0 = __ldg(wv), b1 = __ldg(wv + 1);
 #pragma unroll
                         for (int j = 0; j < 2; ++j) {
-                            const uint32_t cx = j ? cc.z : cc.x;
-                            const int fx = (int)(cx >> 24);
-                            const uint32_t pa = __byte_perm(a0, a1, cx >> 16), pb = __byte_perm(b0, b1, cx >> 16);
-                            const int p00 = (int)(pa & 0xFFu), p01 = (int)((pa >> 8) & 0xFFu);
-                            const int p10 = (int)(pb & 0xFFu), p11 = (int)((pb >> 8) & 0xFFu);
-                            const int h0 = (p00 << 8) + fx * (p01 - p00);
-                            const int h1 = (p10 << 8) + fx * (p11 - p10);
-                            const int acc = (h0 << 8) + (int)fy * (h1 - h0);
+                            const uint32_t sel = j ? cc.z : cc.x, wts = j ? cc.w : cc.y;
+                            // h = 256 p0 + fx (p1 - p0) for the two source rows, then
+                            // (256 - fy) h0 + fy h1 = 256 h0 + fy (h1 - h0), exactly
+                            const uint32_t h0 = __dp4a(__byte_perm(a0, a1, sel), wts, 0u);
+                            const uint32_t h1 = __dp4a(__byte_perm(b0, b1, sel), wts, 0u);
+                            const uint32_t acc = h0 * (256u - fy) + h1 * fy;
                             const int e = 2 * e2 + j;
-                            gw |= (uint32_t)((acc + 32768) >> 16) << (8 * e);
-                            dv[e] = __ldg(drow + (j ? cc.w : cc.y));
+                            gw |= ((acc + 32768u) >> 16) << (8 * e);
+                            dv[e] = __ldg(drow + (j ? (nn >> 16) : (nn & 0xFFFFu)));
                         }
                     }
                     } else {
@@ -297,27 +304,22 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 }
             }
             sm.img[item] = gw;
-            dreg[2 * k] = d01;
-            dreg[2 * k + 1] = d23;
+            reinterpret_cast<uint2*>(sm.dep)[item] = make_uint2(d01, d23);
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+                const uint32_t d = ((hh < 2 ? d01 : d23) >> (16 * (hh & 1))) & 0xFFFFu;
+                const uint32_t key = d >> 10;
+                if (key < 8)
+                    cnt8 += (d ? 1ull : 0ull) << (8 * key);
+                else
+                    atomicAdd(&sm.h1[key], 1u);
+            }
         }
         {
             // coarse histogram of the non-zero depths (bins of 1024 mm): a thread holds 32 depths,
             // so eight 8-bit counters in one 64-bit word count keys 0..7 (depths below 8192 mm);
             // the warp sums them as 16-bit fields (at most 1024 each) and lane 0 adds them to the
             // histogram.  Rarer depths of 8192 mm and beyond count with atomics.
-            unsigned long long cnt8 = 0;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const uint32_t d = (dreg[i] >> (16 * hh)) & 0xFFFFu;
-                    const uint32_t key = d >> 10;
-                    if (key < 8)
-                        cnt8 += (d ? 1ull : 0ull) << (8 * key);
-                    else
-                        atomicAdd(&sm.h1[key], 1u);
-                }
-            }
             const unsigned long long ev = cnt8 & 0x00FF00FF00FF00FFull;          // keys 0, 2, 4, 6
             const unsigned long long od = (cnt8 >> 8) & 0x00FF00FF00FF00FFull;   // keys 1, 3, 5, 7
             const uint32_t s02 = __reduce_add_sync(FULL, (uint32_t)ev);
@@ -382,7 +384,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         if (b1 >= 0) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const uint32_t lo = dreg[i] & 0xFFFFu, hi = dreg[i] >> 16;
+                const uint32_t dw = sm.dep[2 * (tid + (i >> 1) * NT) + (i & 1)];
+                const uint32_t lo = dw & 0xFFFFu, hi = dw >> 16;
                 if (lo && (int)(lo >> 10) == b1) atomicAdd(&sm.h2[lo & 1023u], 1u);
                 if (hi && (int)(hi >> 10) == b1) atomicAdd(&sm.h2[hi & 1023u], 1u);
             }
@@ -428,9 +431,10 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 uint32_t m = 0;
+                const uint2 dd = reinterpret_cast<const uint2*>(sm.dep)[tid + k * NT];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int d = (int)((dreg[2 * k + (e >> 1)] >> (16 * (e & 1))) & 0xFFFFu);
+                    const int d = (int)(((e < 2 ? dd.x : dd.y) >> (16 * (e & 1))) & 0xFFFFu);
                     const int diff = d - med;
                     const bool valid = med >= 0 && d != 0 && diff < a.mask_mm && -diff < a.mask_mm;
                     m |= valid ? (0x80u << (8 * e)) : 0u;
@@ -444,6 +448,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         __syncthreads();
 
         // ---- P5: LBP codes and private histograms, one half cell per thread ---------------
+#pragma unroll
+        for (int w = 0; w < C::HW; ++w) sm.hist[w * NT + tid] = 0;  // (the depths are no longer needed)
         {
             const int c = tid >> 1, h = tid & 1;
             const int cy = c / G, cx = c - cy * G;
