@@ -14,7 +14,7 @@
 //       coarse histogram of 1024 mm bins (eight 8-bit counters per thread in one 64-bit word,
 //       summed over the warp with redux).
 //   P2/P3  radix select of the lower median: the coarse bin holding rank (n-1)/2, then a
-//       1 mm histogram restricted to that bin.
+//       1 mm histogram restricted to that bin (bins are of d - 1, so holes fall outside).
 //   P4  mask bytes (0x80 = valid) from the depths.
 //   P5  one thread per half cell (4 x 8 pixels) walks down its 8 rows with a
 //       3-row sliding window of packed words and computes four codes per step
@@ -99,6 +99,7 @@ struct __align__(16) Smem {
     };
     uint2 colmap[S];                   // taps per crop column, read two at a time (uint4)
     uint2 rowmap[S];                   // taps per crop row
+    unsigned long long ctab[65];       // coarse-histogram increment per key of d - 1 (64: a hole)
     uint16_t ncol[S];                  // nearest depth column per crop column (colmap order)
     uint32_t h1[64];                   // coarse depth histogram: bins of 1024 mm (d >> 10)
     uint32_t h2[1024];                 // fine histogram (d & 1023) inside the median's coarse bin
@@ -110,8 +111,7 @@ struct __align__(16) Smem {
     int info[4];
     uint16_t lut[257];                 // byte offset of each code's counter in a thread's histogram
                                        // (entry 256: the unused bin 59, where invalid centres go)
-    uint32_t qrow[Cfg<S>::G * Cfg<S>::G];  // 65 x valid centres of each cell: its row of qbf
-    uint16_t qbf[65 * 65];             // bf16 bits of the quotient h / n, entry 65 n + h (n, h <= 64)
+    uint16_t qbf[65 * 128];            // bf16 bits of the quotient h / n, entry 128 n + h (n, h <= 64)
 };
 
 template <int S>
@@ -141,14 +141,17 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
     }
     // Quotient table of the bf16 output: a cell has at most 64 centres, so every normalised value
     // is one of the 65 x 65 quotients h / n, computed once per CTA exactly as the other output
-    // types compute them (IEEE single quotient, then round to nearest even bf16).
-    for (int i = tid; i < 65 * 65; i += NT) {
-        const int n = i / 65, hh = i - n * 65;
+    // types compute them (IEEE single quotient, then round to nearest even bf16).  Entry
+    // 128 n + h, so that a staged count with its cell's centre count above it is the index.
+    for (int i = tid; i < 65 * 128; i += NT) {
+        const int n = i >> 7, hh = min(i & 127, 64);
         const float n_f = (float)n, r_f = n ? __frcp_rn(n_f) : 0.f, h_f = (float)hh;
         const float q0 = __fmul_rn(h_f, r_f);
         const float rem = __fmaf_rn(-q0, n_f, h_f);
         sm.qbf[i] = __bfloat16_as_ushort(__float2bfloat16_rn(__fmaf_rn(rem, r_f, q0)));
     }
+
+    for (int i = tid; i < 65; i += NT) sm.ctab[i] = i < 8 ? 1ull << (8 * i) : 0ull;
 
     const bool strict = !(a.flags & RGBD_LBP_GE);
     const bool nbr_ignore = (a.flags & RGBD_LBP_NBR_IGNORE_MASK) != 0;
@@ -308,18 +311,17 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) {
                 const uint32_t d = ((hh < 2 ? d01 : d23) >> (16 * (hh & 1))) & 0xFFFFu;
-                const uint32_t key = d >> 10;
-                if (key < 8)
-                    cnt8 += (d ? 1ull : 0ull) << (8 * key);
-                else
-                    atomicAdd(&sm.h1[key], 1u);
+                const uint32_t key = min((d - 1u) >> 10, 64u);  // a hole (d = 0) wraps to 64
+                cnt8 += sm.ctab[key];
+                if (key - 8u < 56u) atomicAdd(&sm.h1[key], 1u);
             }
         }
         {
-            // coarse histogram of the non-zero depths (bins of 1024 mm): a thread holds 32 depths,
-            // so eight 8-bit counters in one 64-bit word count keys 0..7 (depths below 8192 mm);
-            // the warp sums them as 16-bit fields (at most 1024 each) and lane 0 adds them to the
-            // histogram.  Rarer depths of 8192 mm and beyond count with atomics.
+            // coarse histogram of the non-zero depths, keyed by (d - 1) >> 10 (bins of 1024 mm;
+            // any monotone key serves the select, and this one needs no test for holes): a thread
+            // holds 32 depths, so eight 8-bit counters in one 64-bit word count keys 0..7 (depths
+            // up to 8192 mm), added from a table; the warp sums them as 16-bit fields (at most 1024
+            // each) and lane 0 adds them to the histogram.  Rarer, larger depths count with atomics.
             const unsigned long long ev = cnt8 & 0x00FF00FF00FF00FFull;          // keys 0, 2, 4, 6
             const unsigned long long od = (cnt8 >> 8) & 0x00FF00FF00FF00FFull;   // keys 1, 3, 5, 7
             const uint32_t s02 = __reduce_add_sync(FULL, (uint32_t)ev);
@@ -386,8 +388,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             for (int i = 0; i < 16; ++i) {
                 const uint32_t dw = sm.dep[2 * (tid + (i >> 1) * NT) + (i & 1)];
                 const uint32_t lo = dw & 0xFFFFu, hi = dw >> 16;
-                if (lo && (int)(lo >> 10) == b1) atomicAdd(&sm.h2[lo & 1023u], 1u);
-                if (hi && (int)(hi >> 10) == b1) atomicAdd(&sm.h2[hi & 1023u], 1u);
+                if (((lo - 1u) >> 10) == (uint32_t)b1) atomicAdd(&sm.h2[(lo - 1u) & 1023u], 1u);
+                if (((hi - 1u) >> 10) == (uint32_t)b1) atomicAdd(&sm.h2[(hi - 1u) & 1023u], 1u);
             }
             __syncthreads();
             // rank k1 among the 1024 fine bins: every thread sums its 1024 / NT contiguous bins,
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     if (b2 < 0 && k1 < c + hj) b2 = tid * BPT + j;
                     c += hj;
                 }
-                sm.info[2] = b1 * 1024 + b2;
+                sm.info[2] = b1 * 1024 + b2 + 1;  // keys are of d - 1
             }
             __syncthreads();
             med = sm.info[2];
@@ -428,16 +430,21 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         // ---- P4: depth mask, 0x80 per valid pixel ----------------------------------------
         {
             uint32_t* mw = sm.img + S * S / 4;
+            // d != 0 and |d - med| < mask  <=>  d - lo < width as unsigned numbers, with
+            // lo = max(med - mask + 1, 1) (a hole wraps around) and width = med + mask - lo, or 0
+            // when there is no median (all |d - med| < 65536, so the mask is capped there)
+            const int mk = min(a.mask_mm, 65536);
+            const int lo_i = max(med - mk + 1, 1);
+            const uint32_t lo = (uint32_t)lo_i;
+            const uint32_t width = (med >= 0 && med + mk > lo_i) ? (uint32_t)(med + mk - lo_i) : 0u;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 uint32_t m = 0;
                 const uint2 dd = reinterpret_cast<const uint2*>(sm.dep)[tid + k * NT];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int d = (int)(((e < 2 ? dd.x : dd.y) >> (16 * (e & 1))) & 0xFFFFu);
-                    const int diff = d - med;
-                    const bool valid = med >= 0 && d != 0 && diff < a.mask_mm && -diff < a.mask_mm;
-                    m |= valid ? (0x80u << (8 * e)) : 0u;
+                    const uint32_t d = ((e < 2 ? dd.x : dd.y) >> (16 * (e & 1))) & 0xFFFFu;
+                    m |= (d - lo < width) ? (0x80u << (8 * e)) : 0u;
                 }
                 mw[tid + k * NT] = m;
                 // strict compares with masked neighbours: a grey of 0 never compares greater, so
@@ -536,11 +543,10 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         uint16_t* stg = reinterpret_cast<uint16_t*>(sm.img);
         {
             const int c = tid >> 1, h = tid & 1;
+            const uint32_t nv = sm.cnt[2 * c] + sm.cnt[2 * c + 1];
             if (h == 0) {
-                const uint32_t nv = sm.cnt[2 * c] + sm.cnt[2 * c + 1];
                 sm.nvf[c] = (float)nv;
                 sm.rcp[c] = nv ? __frcp_rn((float)nv) : 0.f;
-                sm.qrow[c] = nv * 65;
             }
             const int w0 = h ? 8 : 0, w1 = h ? C::HW : 8;
             for (int w = w0; w < w1; ++w) {
@@ -548,7 +554,9 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int b = 4 * w + e;
-                    if (b < kBins) stg[c * kBins + b] = (uint16_t)((s >> (8 * e)) & 0xFFu);
+                    // the count (<= 64) with the cell's valid centres above it: the index of
+                    // its quotient in qbf
+                    if (b < kBins) stg[c * kBins + b] = (uint16_t)(((s >> (8 * e)) & 0xFFu) | (nv << 7));
                 }
             }
         }
@@ -562,19 +570,17 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             uint2 hv = make_uint2(0, 0);
             if (j < DIM) {
                 hv = *reinterpret_cast<const uint2*>(stg + j);
-                if (a.feats) *reinterpret_cast<uint2*>(a.feats + (size_t)face * DIM + j) = hv;
+                if (a.feats)
+                    *reinterpret_cast<uint2*>(a.feats + (size_t)face * DIM + j) =
+                        make_uint2(hv.x & 0x007F007Fu, hv.y & 0x007F007Fu);
             }
             if (x_dtype == RGBD_DT_BF16) {
                 // bf16 rows: one table read per value
                 uint32_t pk[2] = {0u, 0u};
                 if (j < DIM) {
-                    const int c0 = j / kBins;
-                    const int split = (c0 + 1) * kBins;
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int cc = (j + e < split) ? c0 : c0 + 1;
-                        const uint32_t hh = ((e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0xFFFFu;
-                        const uint32_t qb = sm.qbf[sm.qrow[cc] + hh];
+                        const uint32_t qb = sm.qbf[((e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0xFFFFu];
                         const float f = __uint_as_float(qb << 16);
                         sq = fmaf(f, f, sq);
                         pk[e >> 1] |= qb << (16 * (e & 1));
@@ -594,7 +600,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     for (int e = 0; e < 4; ++e) {
                         const int cc = (j + e < split) ? c0 : c0 + 1;
                         const float n_f = sm.nvf[cc], r_f = sm.rcp[cc];
-                        const float h_f = (float)(((e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0xFFFFu);
+                        const float h_f = (float)(((e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0x7Fu);
                         const float q0 = __fmul_rn(h_f, r_f);
                         const float rem = __fmaf_rn(-q0, n_f, h_f);
                         x[e] = __fmaf_rn(rem, r_f, q0);
