@@ -109,6 +109,7 @@ struct __align__(16) Smem {
     float red[Cfg<S>::NT / 32];
     uint32_t wsum[Cfg<S>::NT / 32];   // per-warp totals of the fine median histogram
     int info[4];
+    rgbd_rect nrect;                   // the next face's rect, copied in during the current face
     uint16_t lut[257];                 // byte offset of each code's counter in a thread's histogram
                                        // (entry 256: the unused bin 59, where invalid centres go)
     uint16_t qbf[65 * 128];            // bf16 bits of the quotient h / n, entry 128 n + h (n, h <= 64)
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         const uint16_t* dsrc = a.depth;
         int64_t aff[6] = {0, 0, 0, 0, 0, 0};
         if (a.rects) {
-            r = a.rects[face];
+            r = face == (int)blockIdx.x ? a.rects[face] : sm.nrect;
             ok = r.frame >= 0 && r.frame < a.n_frames && r.w > 0 && r.h > 0;
             if (!ok && tid == 0) atomicOr(a.status, RGBD_STATUS_BAD_RECT);
             if (ok) {
@@ -226,6 +227,11 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         // ---- P1: resample; grey to shared memory, depth to registers ----------------------
         // All taps are gathered first (independent loads, no warp-synchronous step in
         // between), then the high-byte histogram of the non-zero depths is built.
+        // the next face is claimed now (the atomic's latency hides behind P1) and published at
+        // the end of P1; its rect is copied into shared memory asynchronously during P5
+        int next_face = 0;
+        if (tid == 0)
+            next_face = a.face_counter ? (int)gridDim.x + (int)atomicAdd(a.face_counter, 1u) : face + (int)gridDim.x;
         unsigned long long cnt8 = 0;  // coarse depth histogram, see below
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -336,6 +342,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     if (c8[k]) atomicAdd(&sm.h1[k], c8[k]);
             }
         }
+        if (tid == 0) sm.info[3] = next_face;
         __syncthreads();
 
         // ---- P2: coarse bin of the lower median (rank (n-1)/2 of the non-zero depths) -----
@@ -455,6 +462,14 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         __syncthreads();
 
         // ---- P5: LBP codes and private histograms, one half cell per thread ---------------
+        if (tid == 0 && a.rects && sm.info[3] < a.n) {
+            const int* src = reinterpret_cast<const int*>(a.rects + sm.info[3]);
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&sm.nrect);
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4u * i), "l"(src + i) : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
 #pragma unroll
         for (int w = 0; w < C::HW; ++w) sm.hist[w * NT + tid] = 0;  // (the depths are no longer needed)
         {
@@ -656,8 +671,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 a.xsq[face] = t;
             }
         }
-        if (tid == 0)
-            sm.info[3] = a.face_counter ? (int)gridDim.x + (int)atomicAdd(a.face_counter, 1u) : face + (int)gridDim.x;
+        if (tid == 0 && a.rects) asm volatile("cp.async.wait_all;" ::: "memory");  // the next rect has landed
         __syncthreads();
         face = sm.info[3];
     }
