@@ -2,21 +2,21 @@
 // function of Section 2.5, S_c = sum_i a_ci exp(-gamma |x - sv_i|^2) + b_c, for BF16, FP8 E4M3
 // (per-tensor scales) and TF32 operands with fp32 accumulation in tensor memory.
 //
-// One CTA (11 warps) owns 128 feature rows and a contiguous range ("split") of 256-wide SV tiles:
+// One CTA (19 warps) owns 128 feature rows and a contiguous range ("split") of 256-wide SV tiles:
 //   warp 0      TMA producer of the main ring: per k-block (128 B of K per row, 128B-swizzled)
 //               the 128-row X block and the SV block (4 stages of 48 KB; 6 of 32 KB in 2-CTA pairs,
-//               where each CTA holds half of the SV tile).
+//               where each CTA holds half of the SV tile and stages are released two at a time).
 //   warp 1      TMEM owner and MMA issuer (one thread; in 2-CTA pairs only CTA 0's):
 //                 G (128 x 256 fp32, TMEM)  = X . SV_t^T over all k-blocks   (N = 256 MMAs)
 //                 D (128 x C_pad fp32, TMEM) += F_q . a_q^T  for every 64-column chunk q of F,
 //               with F read from tensor memory (A operand) and a from shared memory.
 //   warp 2      TMA producer of the bf16 coefficient chunks a[c][64 SVs] (2-slot ring).
-//   warps 3-10  epilogue, two sets of four warps (one per TMEM lane quarter); set k handles the
-//               64-column chunks k and k + 2 of every tile.  One thread per row reads G with
-//               tcgen05.ld, forms d^2 = |x|^2 + |sv|^2 - 2 G and F = expm1(-gamma (d^2 - r)) in
-//               bf16, and stores F with tcgen05.st into its slot (two slots of 32 packed columns)
-//               for the second MMA.  r is the row's mean d^2 over chunks 0
-//               and 2 of the split's first tile; since exp(-gamma d^2) = exp(-gamma r) (1 + F),
+//   warps 3-18  epilogue, four sets of four warps (one per TMEM lane quarter); set k handles the
+//               64-column chunk k of every tile.  One thread per row reads its chunk of G with
+//               tcgen05.ld and releases G, then forms d^2 = |x|^2 + |sv|^2 - 2 G and
+//               F = expm1(-gamma (d^2 - r)) in bf16, and stores F with tcgen05.st into its slot
+//               (two slots of 32 packed columns) for the second MMA.  r is the row's mean d^2 over
+//               chunks 0 and 2 of the split's first tile; since exp(-gamma d^2) = exp(-gamma r) (1 + F),
 //                 S_c = sum_splits exp(-gamma r_s) (sum_{i in s} a_ci + D_s[c]) + b_c,
 //               and F keeps the small per-SV variation at full relative precision (gamma d^2 is
 //               ~2e-4 for gamma = 1/dim, so exp() itself is flat to 1e-4).
@@ -378,6 +378,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     constexpr int CG = PAIR ? 2 : 1;
     constexpr uint32_t F_SLOT = SPLIT2 ? 64u : 32u;  // TMEM columns per F slot
     using L = Lay<MODE, SPLIT2>;
+    // Pairs release ring stages two at a time: a 2-CTA multicast commit per k-block cost ~5 % of
+    // the kernel (the ring turned over slower than its copies land).  Single CTAs, with a 4-stage
+    // ring, keep one commit per stage.
+    constexpr int GRP = (MODE == MODE_PAIR && L::STAGES % 2 == 0) ? 2 : 1;  // stages released per commit
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned for the 128B swizzle atoms
@@ -457,7 +461,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const int pass = kt / p.k_blocks, kb = kt - pass * p.k_blocks;
                     const CUtensorMap* mx = (pass == 2) ? &tm_x2 : &tm_x;
                     const CUtensorMap* msv = (pass == 1) ? &tm_sv2 : &tm_sv;
-                    if (!bar_spin<PAIR>(bar(B_EMPTY + stage), phase ^ 1u, abort_flag, p.status)) {
+                    // the first stage of a group waits for the group's release (EMPTY slot stage / GRP)
+                    if ((GRP == 1 || stage % GRP == 0) &&
+                        !bar_spin<PAIR>(bar(B_EMPTY + stage / GRP), phase ^ 1u, abort_flag, p.status)) {
                         alive = false;
                         break;
                     }
@@ -611,12 +617,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                     for (int ks = 1; ks < 4; ++ks)
                         mma_issue<CG, KIND>(tmem, a0 + 2u * ks, b0 + 2u * ks, p.idesc_main, 1u);
-                    if (PAIR)
-                        tc_commit2_mc(bar(B_EMPTY + stage), (uint16_t)0x3);
-                    else if (MC)
-                        tc_commit_mc(bar(B_EMPTY + stage), (uint16_t)0x3);
-                    else
-                        tc_commit(bar(B_EMPTY + stage));
+                    // release a group after its last stage (and after the split's last k-block)
+                    if (GRP == 1 || stage % GRP == GRP - 1 || (u == U - 1 && kt == p.passes * p.k_blocks - 1)) {
+                        if (PAIR)
+                            tc_commit2_mc(bar(B_EMPTY + stage / GRP), (uint16_t)0x3);
+                        else if (MC)
+                            tc_commit_mc(bar(B_EMPTY + stage / GRP), (uint16_t)0x3);
+                        else
+                            tc_commit(bar(B_EMPTY + stage / GRP));
+                    }
                     if (++stage == L::STAGES) {
                         stage = 0;
                         phase ^= 1u;
