@@ -378,9 +378,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     constexpr int CG = PAIR ? 2 : 1;
     constexpr uint32_t F_SLOT = SPLIT2 ? 64u : 32u;  // TMEM columns per F slot
     using L = Lay<MODE, SPLIT2>;
-    // Pairs release ring stages two at a time: a 2-CTA multicast commit per k-block cost ~5 % of
-    // the kernel (the ring turned over slower than its copies land).  Single CTAs, with a 4-stage
-    // ring, keep one commit per stage.
+    // Pairs fill and release ring stages two at a time (one FULL and one EMPTY barrier per
+    // group): a 2-CTA multicast commit per k-block cost ~5 % of the kernel (the ring turned over
+    // slower than its copies land).  Single CTAs, with a 4-stage ring, keep one per stage.
     constexpr int GRP = (MODE == MODE_PAIR && L::STAGES % 2 == 0) ? 2 : 1;  // stages released per commit
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -469,8 +469,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                     const uint32_t sa = base + (uint32_t)stage * L::STAGE;
                     if (PAIR) {
-                        const uint32_t fb = map_rank0(bar(B_FULL + stage));
-                        if (crank == 0) bar_arrive_tx(bar(B_FULL + stage), 2u * L::STAGE);
+                        const uint32_t fb = map_rank0(bar(B_FULL + stage / GRP));
+                        // one FULL barrier per group of stages: the group's first stage arms it
+                        // for all the group's copies (fewer when the split's k-blocks run out)
+                        if (crank == 0 && stage % GRP == 0) {
+                            const int left = U * KT - (u * KT + kt);  // k-blocks still to load
+                            const uint32_t nst = (uint32_t)min(GRP, left);
+                            bar_arrive_tx(bar(B_FULL + stage / GRP), 2u * L::STAGE * nst);
+                        }
                         tma_load_2d_pair(sa, mx, kb * p.k_elems, m0, fb);
                         tma_load_2d_pair(sa + X_TILE, msv, kb * p.k_elems, n0 + (int)crank * (BN / 2), fb);
                     } else {
@@ -501,7 +507,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const uint64_t tq = globaltimer();
                 for (int s = 0; s < L::STAGES; ++s)
                     if (armed & (1u << s))
-                        while (!bar_try<PAIR>(bar(B_FULL + s), (armed_par >> s) & 1u) &&
+                        while (!bar_try<PAIR>(bar(B_FULL + s / GRP), (armed_par >> s) & 1u) &&
                                globaltimer() - tq < WAIT_NS) {
                         }
             }
@@ -605,7 +611,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     // so the ready case costs one barrier test, the stage's TMA data needs no
                     // tcgen05 fence (the barrier orders it), and finished F chunks are serviced only
                     // every 8 k-blocks (the epilogue waits two chunks back).
-                    if (!bar_try<PAIR>(bar(B_FULL + stage), phase) && !wait_servicing(bar(B_FULL + stage), phase)) {
+                    // one wait per group of stages (its FULL barrier counts all its copies)
+                    if (stage % GRP == 0 && !bar_try<PAIR>(bar(B_FULL + stage / GRP), phase) &&
+                        !wait_servicing(bar(B_FULL + stage / GRP), phase)) {
                         alive = false;
                         break;
                     }
