@@ -19,7 +19,9 @@
 //   P5  one thread per half cell (4 x 8 pixels) walks down its 8 rows with a
 //       3-row sliding window of packed words and computes four codes per step
 //       with byte-SIMD compares; codes go through the uniform table into a
-//       thread-private 8-bit histogram (no atomics, no bank conflicts).
+//       thread-private 8-bit histogram (no atomics, no bank conflicts).  Under the
+//       default rule an invalid centre compares as grey 255 and so has code 0; P6
+//       subtracts the cell's invalid centres from bin 0.
 //   P6/P7  half-cell histograms are summed into a uint16 staging row, which is
 //       written out coalesced together with the normalised row and its norm (bf16 rows
 //       read each quotient h / n from a per-CTA table of the 65 x 65 possible values).
@@ -92,7 +94,9 @@ struct Cfg {
 
 template <int S>
 struct __align__(16) Smem {
-    uint32_t img[2 * S * S / 4];       // grey words, then mask words; later the uint16 staging row
+    // grey words with a one-word / one-row clamp-to-edge border ((S + 2) rows of S / 4 + 2
+    // words), then mask words; later the uint16 staging row
+    uint32_t img[(S + 2) * (S / 4 + 2) + S * S / 4];
     union {
         uint32_t hist[Cfg<S>::HW * Cfg<S>::NT];  // P5-P6: thread-private 8-bit counts, word (bin/4)*NT + t
         uint32_t dep[S * S / 2];                 // P1-P4: the crop's depths, two per word, by item
@@ -119,6 +123,8 @@ template <int S>
 __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(LbpArgs a) {
     using C = Cfg<S>;
     constexpr int NT = C::NT, SW = C::SW, G = C::G, DIM = C::DIM;
+    constexpr int SP = SW + 2;               // words per row of the bordered grey plane
+    constexpr int MW_OFF = (S + 2) * SP;     // the mask plane follows it
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<S>& sm = *reinterpret_cast<Smem<S>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     d23 = dv[2] | (dv[3] << 16);
                 }
             }
-            sm.img[item] = gw;
+            sm.img[(v + 1) * SP + q + 1] = gw;
             reinterpret_cast<uint2*>(sm.dep)[item] = make_uint2(d01, d23);
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) {
@@ -436,7 +442,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
 
         // ---- P4: depth mask, 0x80 per valid pixel ----------------------------------------
         {
-            uint32_t* mw = sm.img + S * S / 4;
+            uint32_t* mw = sm.img + MW_OFF;
             // d != 0 and |d - med| < mask  <=>  d - lo < width as unsigned numbers, with
             // lo = max(med - mask + 1, 1) (a hole wraps around) and width = med + mask - lo, or 0
             // when there is no median (all |d - med| < 65536, so the mask is capped there)
@@ -454,9 +460,28 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     m |= (d - lo < width) ? (0x80u << (8 * e)) : 0u;
                 }
                 mw[tid + k * NT] = m;
+                const int item = tid + k * NT, v = item / SW, q = item - v * SW;
+                uint32_t* gp = sm.img + (v + 1) * SP + q + 1;
+                uint32_t g = *gp;
                 // strict compares with masked neighbours: a grey of 0 never compares greater, so
                 // zeroing the invalid pixels once replaces the per-neighbour masks of P5
-                if (masked_grey) sm.img[tid + k * NT] &= (m >> 7) * 0xFFu;
+                if (masked_grey) {
+                    g &= (m >> 7) * 0xFFu;
+                    *gp = g;
+                }
+                // the border repeats the edge pixels (clamp-to-edge neighbours)
+                if (q == 0) gp[-1] = g << 24;
+                if (q == SW - 1) gp[1] = g >> 24;
+                if (v == 0) {
+                    gp[-SP] = g;
+                    if (q == 0) gp[-SP - 1] = g << 24;
+                    if (q == SW - 1) gp[-SP + 1] = g >> 24;
+                }
+                if (v == S - 1) {
+                    gp[SP] = g;
+                    if (q == 0) gp[SP - 1] = g << 24;
+                    if (q == SW - 1) gp[SP + 1] = g >> 24;
+                }
             }
         }
         __syncthreads();
@@ -480,9 +505,16 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             const bool le = wc == 0, re = wc == SW - 1;
             const int wl = le ? wc : wc - 1, wr = re ? wc : wc + 1;
             const uint32_t* GW = sm.img;
-            const uint32_t* MW = sm.img + S * S / 4;
+            const uint32_t* MW = sm.img + MW_OFF;
             // Words holding pixels (x-1 .. x+2), (x .. x+3), (x+1 .. x+4) of a row; past the crop
-            // edge a neighbour repeats the edge pixel.
+            // edge a neighbour repeats the edge pixel (the grey plane's border holds the repeats).
+            auto row3g = [&](int row, uint32_t& L, uint32_t& M, uint32_t& R) {
+                const uint32_t* p = GW + (row + 1) * SP + wc + 1;
+                const uint32_t c0 = p[0];
+                L = __byte_perm(p[-1], c0, 0x6543);
+                M = c0;
+                R = __byte_perm(c0, p[1], 0x4321);
+            };
             auto row3 = [&](const uint32_t* base, int row, uint32_t& L, uint32_t& M, uint32_t& R) {
                 row = min(max(row, 0), S - 1);
                 const uint32_t* p = base + row * SW;
@@ -498,35 +530,36 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             uint8_t* hb_t = reinterpret_cast<uint8_t*>(sm.hist) + 4 * tid;  // this thread's counters
             if (masked_grey) {
                 // invalid pixels read as grey 0 (P4): no neighbour masks, only the centre's
-                row3(GW, r0 - 1, gUL, gUC, gUR);
-                row3(GW, r0, gCL, gCC, gCR);
+                row3g(r0 - 1, gUL, gUC, gUR);
+                row3g(r0, gCL, gCC, gCR);
 #pragma unroll 2
                 for (int i = 0; i < 8; ++i) {
-                    row3(GW, r0 + i + 1, gDL, gDC, gDR);
+                    row3g(r0 + i + 1, gDL, gDC, gDR);
                     const uint32_t mC = MW[(r0 + i) * SW + wc];
-                    const uint32_t cb = (gCC & 0x7F7F7F7Fu) + 0x01010101u;
-                    const uint32_t code = (cmp_msb(gUL, gCC, cb) >> 7) | (cmp_msb(gUC, gCC, cb) >> 6) |
-                                          (cmp_msb(gUR, gCC, cb) >> 5) | (cmp_msb(gCR, gCC, cb) >> 4) |
-                                          (cmp_msb(gDR, gCC, cb) >> 3) | (cmp_msb(gDC, gCC, cb) >> 2) |
-                                          (cmp_msb(gDL, gCC, cb) >> 1) | cmp_msb(gCL, gCC, cb);
+                    // an invalid centre compares as grey 255, so no neighbour is greater and its
+                    // code is 0; P6 takes the invalid centres back out of bin U(0) = 0
+                    const uint32_t inv = ~mC & 0x80808080u;
+                    const uint32_t gc = gCC | inv | (inv - (inv >> 7));
+                    const uint32_t cb = (gc & 0x7F7F7F7Fu) + 0x01010101u;
+                    const uint32_t code = (cmp_msb(gUL, gc, cb) >> 7) | (cmp_msb(gUC, gc, cb) >> 6) |
+                                          (cmp_msb(gUR, gc, cb) >> 5) | (cmp_msb(gCR, gc, cb) >> 4) |
+                                          (cmp_msb(gDR, gc, cb) >> 3) | (cmp_msb(gDC, gc, cb) >> 2) |
+                                          (cmp_msb(gDL, gc, cb) >> 1) | cmp_msb(gCL, gc, cb);
                     nvalid += __popc(mC);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const uint32_t idx = ((mC >> (8 * e + 7)) & 1u) ? ((code >> (8 * e)) & 0xFFu) : 256u;
-                        hb_t[sm.lut[idx]] += 1;
-                    }
+                    for (int e = 0; e < 4; ++e) hb_t[sm.lut[(code >> (8 * e)) & 0xFFu]] += 1;
                     gUL = gCL; gUC = gCC; gUR = gCR; gCL = gDL; gCC = gDC; gCR = gDR;
                 }
                 sm.cnt[tid] = nvalid;
             } else {
             uint32_t mUL, mUC, mUR, mCL, mCC, mCR, mDL, mDC, mDR;
-            row3(GW, r0 - 1, gUL, gUC, gUR);
+            row3g(r0 - 1, gUL, gUC, gUR);
             row3(MW, r0 - 1, mUL, mUC, mUR);
-            row3(GW, r0, gCL, gCC, gCR);
+            row3g(r0, gCL, gCC, gCR);
             row3(MW, r0, mCL, mCC, mCR);
 #pragma unroll 2
             for (int i = 0; i < 8; ++i) {
-                row3(GW, r0 + i + 1, gDL, gDC, gDR);
+                row3g(r0 + i + 1, gDL, gDC, gDR);
                 row3(MW, r0 + i + 1, mDL, mDC, mDR);
                 const uint32_t NM = 0x80808080u;
                 const uint32_t cb = (gCC & 0x7F7F7F7Fu) + (strict ? 0x01010101u : 0u);
@@ -565,7 +598,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             }
             const int w0 = h ? 8 : 0, w1 = h ? C::HW : 8;
             for (int w = w0; w < w1; ++w) {
-                const uint32_t s = sm.hist[w * NT + 2 * c] + sm.hist[w * NT + 2 * c + 1];
+                uint32_t s = sm.hist[w * NT + 2 * c] + sm.hist[w * NT + 2 * c + 1];
+                if (masked_grey && w == 0) s -= 64u - nv;  // the invalid centres counted as code 0
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int b = 4 * w + e;
