@@ -25,6 +25,8 @@
 //   P6/P7  half-cell histograms are summed into a uint16 staging row, which is
 //       written out coalesced together with the normalised row and its norm (bf16 rows
 //       read each quotient h / n from a per-CTA table of the 65 x 65 possible values).
+//       P7 first asks L2 for the next face's source rows (its rect was copied in during P5),
+//       so that face's P1 gathers find them there.
 // Everything up to A4 is exact integer arithmetic.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -59,6 +61,30 @@ __device__ __forceinline__ uint2 make_tap(int64_t q, int lim) {
     const int b = (int)(f0 + 1 < 0 ? 0 : (f0 + 1 > hi ? hi : f0 + 1));
     const int n = (int)(nn < 0 ? 0 : (nn > hi ? hi : nn));
     return make_uint2((uint32_t)a | ((uint32_t)(b - a) << 16) | ((uint32_t)frac << 24), (uint32_t)n);
+}
+
+// Asks L2 for the source rows of a face rect (grey and depth, each row's span widened by one
+// pixel for the bilinear taps and clamped to the frame): one prefetch per 128 bytes, every
+// address inside its row's span.  Threads pair up per row: even threads take the grey span,
+// odd ones the depth span.
+__device__ __forceinline__ void prefetch_rect_rows(const uint8_t* grey, const uint16_t* depth, int H, int W,
+                                                   const rgbd_rect& rn, int tid, int nt) {
+    const int x0 = max(rn.x - 1, 0), x1 = min(rn.x + rn.w + 1, W);
+    const int y0 = max(rn.y - 1, 0), y1 = min(rn.y + rn.h + 1, H);
+    if (x1 <= x0 || y1 <= y0) return;
+    const size_t plane = (size_t)H * W;
+    const bool dep = tid & 1;
+    const uint8_t* base = dep ? reinterpret_cast<const uint8_t*>(depth + (size_t)rn.frame * plane)
+                              : grey + (size_t)rn.frame * plane;
+    const size_t esz = dep ? 2 : 1;
+    for (int y = y0 + (tid >> 1); y < y1; y += nt >> 1) {
+        const uint8_t* first = base + ((size_t)y * W + x0) * esz;
+        const uint8_t* last = base + ((size_t)y * W + x1) * esz - 1;
+        for (const uint8_t* pp = first;; pp += 128) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pp < last ? pp : last));
+            if (pp >= last - 127) break;
+        }
+    }
 }
 
 // Bilinear grey sample with Q8 weights (they sum to 2^16), rounded half up.
@@ -585,6 +611,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             sm.cnt[tid] = nvalid;
             }
         }
+        if (tid == 0 && a.rects) asm volatile("cp.async.wait_all;" ::: "memory");  // the next rect has landed
         __syncthreads();
 
         // ---- P6: sum the two half-cell histograms into a uint16 staging row ----------------
@@ -612,6 +639,12 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         __syncthreads();
 
         // ---- P7: coalesced output of counts, normalised row and its squared norm ----------
+        // first ask L2 for the next face's source rows, a face ahead of its P1 gathers
+        if (a.rects && !a.affine && sm.info[3] < a.n) {
+            const rgbd_rect rn = sm.nrect;
+            if (rn.frame >= 0 && rn.frame < a.n_frames && rn.w > 0 && rn.h > 0)
+                prefetch_rect_rows(a.grey, a.depth, a.H, a.W, rn, tid, NT);
+        }
         float sq = 0.f;
         const int len4 = (x_dtype ? a.k_pad : DIM) / 4;
         for (int j4 = tid; j4 < len4; j4 += NT) {
@@ -705,7 +738,6 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 a.xsq[face] = t;
             }
         }
-        if (tid == 0 && a.rects) asm volatile("cp.async.wait_all;" ::: "memory");  // the next rect has landed
         __syncthreads();
         face = sm.info[3];
     }
