@@ -138,6 +138,7 @@ struct __align__(16) Smem {
     float rcp[Cfg<S>::G * Cfg<S>::G];  // ... and its IEEE reciprocal (0 for an empty cell)
     float red[Cfg<S>::NT / 32];
     uint32_t wsum[Cfg<S>::NT / 32];   // per-warp totals of the fine median histogram
+    uint32_t sink[32];                 // target of the border stores of non-edge lanes
     int info[4];
     rgbd_rect nrect;                   // the next face's rect, copied in during the current face
     uint16_t lut[257];                 // byte offset of each code's counter in a thread's histogram
@@ -495,18 +496,18 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     g &= (m >> 7) * 0xFFu;
                     *gp = g;
                 }
-                // the border repeats the edge pixels (clamp-to-edge neighbours)
-                if (q == 0) gp[-1] = g << 24;
-                if (q == SW - 1) gp[1] = g >> 24;
-                if (v == 0) {
-                    gp[-SP] = g;
-                    if (q == 0) gp[-SP - 1] = g << 24;
-                    if (q == SW - 1) gp[-SP + 1] = g >> 24;
-                }
-                if (v == S - 1) {
-                    gp[SP] = g;
-                    if (q == 0) gp[SP - 1] = g << 24;
-                    if (q == SW - 1) gp[SP + 1] = g >> 24;
+                // the border repeats the edge pixels (clamp-to-edge neighbours); branch-free:
+                // lanes away from the left and right edges store into a sink word
+                {
+                    const bool le = q == 0, re = q == SW - 1;
+                    uint32_t* side = le ? gp - 1 : (re ? gp + 1 : sm.sink + lane);
+                    const uint32_t pv = le ? (g << 24) : (g >> 24);
+                    *side = pv;
+                    if (v == 0 || v == S - 1) {  // the border rows
+                        const int dv = v == 0 ? -SP : SP;
+                        gp[dv] = g;
+                        *((le || re) ? side + dv : sm.sink + lane) = pv;  // corner words
+                    }
                 }
             }
         }

@@ -698,7 +698,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         };
         for (int u = 0; u < U && alive; ++u) {
             const int n0 = (t0 + u) * BN;
-            if (!wait_warp(bar(B_GFULL), (uint32_t)(u & 1))) {
+            // the tile's G: lane 0 polls with short sleeps (a thread suspended in try_wait wakes
+            // late, and plain spinning takes issue slots from the warps computing F), then falls
+            // back to the bounded wait
+            bool g_ok = true;
+            if (lane == 0) {
+                int polls = 0;
+                while (!bar_test<PAIR>(bar(B_GFULL), (uint32_t)(u & 1))) {
+                    __nanosleep(64);
+                    if (++polls > (1 << 20)) {
+                        g_ok = bar_wait<PAIR>(bar(B_GFULL), (uint32_t)(u & 1), abort_flag, p.status);
+                        break;
+                    }
+                }
+            }
+            if (!__shfl_sync(0xFFFFFFFFu, g_ok ? 1 : 0, 0)) {
                 alive = false;
                 break;
             }

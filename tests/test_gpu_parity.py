@@ -107,6 +107,18 @@ def test_ragged_batch_and_edge_cases(B, ctx, orc, crop):
     assert (x.cpu().numpy()[:, :dim].view(np.uint32) == x32.view(np.uint32)).all()
 
 
+@pytest.mark.parametrize("W", [322, 318])
+def test_frame_width_not_a_multiple_of_4(B, ctx, orc, W):
+    """Frame rows that are not word-aligned take the byte-gather resample (the 8-byte grey
+    windows need 4-byte aligned rows); rects reach the right edge."""
+    g, d, r = synth.frames_with_rects(57, 2, 6, 20, 200, H=200, W=W)
+    r = np.concatenate([r, np.array([(0, W - 30, 5, 30, 60), (1, W - 200, 100, 200, 100)], synth.RECT_DTYPE)])
+    for crop in (64, 128):
+        want = orc.features_batch(g, d, r, crop)
+        f, _, _ = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=crop)
+        assert (host_u16(f) == want).all(), crop
+
+
 @pytest.mark.parametrize("flags", [1, 2, 3])
 def test_lbp_option_flags(B, ctx, orc, flags):
     g, d, r = synth.frames_with_rects(5, 2, 4, 40, 200, H=240, W=320)
