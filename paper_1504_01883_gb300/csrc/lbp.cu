@@ -647,7 +647,33 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 prefetch_rect_rows(a.grey, a.depth, a.H, a.W, rn, tid, NT);
         }
         float sq = 0.f;
-        const int len4 = (x_dtype ? a.k_pad : DIM) / 4;
+        const bool wide = x_dtype == RGBD_DT_BF16 && (a.k_pad & 7) == 0 && (DIM & 7) == 0 &&
+                          ((reinterpret_cast<size_t>(a.feats) | reinterpret_cast<size_t>(a.x_out)) & 15) == 0;
+        if (wide) {
+            // bf16 rows, 8 values per thread step (16-byte loads and stores)
+            for (int j8 = tid; j8 < a.k_pad / 8; j8 += NT) {
+                const int j = 8 * j8;
+                uint4 hv = make_uint4(0u, 0u, 0u, 0u);
+                uint32_t pk[4] = {0u, 0u, 0u, 0u};
+                if (j < DIM) {
+                    hv = *reinterpret_cast<const uint4*>(stg + j);
+                    if (a.feats)
+                        *reinterpret_cast<uint4*>(a.feats + (size_t)face * DIM + j) =
+                            make_uint4(hv.x & 0x007F007Fu, hv.y & 0x007F007Fu, hv.z & 0x007F007Fu, hv.w & 0x007F007Fu);
+                    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const uint32_t qb = sm.qbf[(hw[e >> 1] >> (16 * (e & 1))) & 0xFFFFu];
+                        const float f = __uint_as_float(qb << 16);
+                        sq = fmaf(f, f, sq);
+                        pk[e >> 1] |= qb << (16 * (e & 1));
+                    }
+                }
+                *reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(a.x_out) + (size_t)face * a.k_pad + j) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        const int len4 = wide ? 0 : (x_dtype ? a.k_pad : DIM) / 4;
         for (int j4 = tid; j4 < len4; j4 += NT) {
             const int j = 4 * j4;
             uint2 hv = make_uint2(0, 0);
