@@ -131,8 +131,8 @@ struct __align__(16) Smem {
     uint2 rowmap[S];                   // taps per crop row
     unsigned long long ctab[65];       // coarse-histogram increment per key of d - 1 (64: a hole)
     uint16_t ncol[S];                  // nearest depth column per crop column (colmap order)
-    uint32_t h1[64];                   // coarse depth histogram: bins of 1024 mm (d >> 10)
-    uint32_t h2[1024];                 // fine histogram (d & 1023) inside the median's coarse bin
+    uint32_t h1[64];                   // coarse depth histogram: key (d - 1) >> 10 (1024 mm bins)
+    uint32_t h2[1024];                 // fine histogram ((d - 1) & 1023) inside the median's coarse bin
     uint32_t cnt[Cfg<S>::NT];          // valid centres per half cell
     float nvf[Cfg<S>::G * Cfg<S>::G];  // valid centres per cell (as float) ...
     float rcp[Cfg<S>::G * Cfg<S>::G];  // ... and its IEEE reciprocal (0 for an empty cell)
@@ -142,7 +142,8 @@ struct __align__(16) Smem {
     int info[4];
     rgbd_rect nrect;                   // the next face's rect, copied in during the current face
     uint16_t lut[257];                 // byte offset of each code's counter in a thread's histogram
-                                       // (entry 256: the unused bin 59, where invalid centres go)
+                                       // (entry 256: the unused bin 59, where invalid centres go
+                                       // under the rules other than the default one)
     uint16_t qbf[65 * 128];            // bf16 bits of the quotient h / n, entry 128 n + h (n, h <= 64)
 };
 

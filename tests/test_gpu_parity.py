@@ -301,6 +301,28 @@ def test_tensor_core_pairing_modes(B, ctx, orc, dt, mc):
     assert err <= bound, err
 
 
+@pytest.mark.parametrize("splits", [1, 3])
+def test_fp8_odd_k_block_count_in_pairs(B, ctx, orc, splits):
+    """2-CTA pairs fill and release ring stages two at a time; an FP8 row of 3 x 3 cells
+    (531 values, k_pad 640 = 5 k-blocks of 128 bytes) with 3 SV tiles per split ends a split on
+    a half group (15 k-blocks), which the FULL/EMPTY bookkeeping must close."""
+    X, SV, a, b, gamma = _scoring_problem(91 + splits, 300, 700, 12, cells=9)
+    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype="fp8")
+    x, q = B.lbp_normalize_features(ctx, dev_u16(X), "fp8", x_scale=448.0)
+    ctx.set_tuning(B.TUNE_TC_SPLITS, splits)
+    ctx.set_tuning(B.TUNE_TC_MULTICAST, 3)
+    try:
+        s, lab = B.svm_score(ctx, model, x, q, x_scale=448.0)
+        assert ctx.status() == 0
+    finally:
+        ctx.set_tuning(B.TUNE_TC_SPLITS, 0)
+        ctx.set_tuning(B.TUNE_TC_MULTICAST, 0)
+    x64, sv64 = orc.normalize_f64(X), orc.normalize_f64(SV)
+    ref = orc.svm_rbf(x64, sv64, a, b, gamma)
+    err = rel_score_error(s.cpu().numpy(), ref, rbf_error_scale(x64, sv64, a, b, gamma))
+    assert err <= 1e-3, err
+
+
 @pytest.mark.parametrize("splits,mc", [(1, 2), (3, 1), (8, 2), (2, 3), (8, 3)])
 def test_tuning_changes_layout_not_results(B, ctx, orc, splits, mc):
     """Forced SV splits / multicast (the autotuner's knobs) keep the scores within tolerance."""
