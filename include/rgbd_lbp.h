@@ -229,8 +229,8 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
                        void* x_out, int k_pad, float x_scale, float* xsq_out, void* stream);
 
 /* With flags & RGBD_LBP_FACE_HIST256 the same call computes the paper's own face descriptor
- * (Section 3: after the LBP codes, "histogram is calculated ranging from 0 to 255, for each
- * face"): crop any size 8..255 (the paper resizes faces to 200x200), cell == crop, and feats
+ * (Section 3: one histogram of the raw 8-bit LBP codes, bins 0..255, per face): crop any size
+ * 8..255 (the paper resizes faces to 200x200), cell == crop, and feats
  * is uint16 [n][256], bin = raw code.  Mask, codes and normalisation are as above (one cell). */
 
 /* A5 alone: per-cell normalisation of count rows that came from elsewhere (a
