@@ -315,8 +315,8 @@ int svm_train_rbf(rgbd_ctx* ctx, const float* x, const float* xsq, int n, int k_
 /* ======================================================================================= */
 
 /* For each face of the previous frame, the face of the current frame whose rect centre is
- * nearest to its own (Section 2.3: person A's face in the next frame is the detected face
- * whose centre is nearest to A's previous centre).  The `frame` field of each rect is the
+ * nearest to its own (Section 2.3: a person's face in the following frame is the detection
+ * whose centre lies closest to that person's previous centre).  The `frame` field of each rect is the
  * camera stream id: faces only match faces of the same stream.
  *   prev  rgbd_rect [n_prev], cur rgbd_rect [n_cur] (device)
  *   match int32 [n_prev] (device): index into cur, or -1 when the stream has no current
