@@ -273,7 +273,7 @@ def main():
                     help="run the timed steps strictly one after the other (by default step i+1's feature "
                          "kernel overlaps step i's scoring)")
     ap.add_argument("--tune", default=None, metavar="CTAS,SPLITS,PAIRING",
-                    help="fixed launch layout (K1 CTAs/SM, scoring splits, CTA pairing 1=multicast 2=none "
+                    help="fixed launch layout (K1 CTAs/SM, scoring splits, CTA pairing 2=none "
                          "3=2-CTA MMA) instead of the autotuner, e.g. to profile the layout a previous run chose")
     ap.add_argument("--ref-crops-per-step", type=int, default=8)
     ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision", "roi", "train"],
@@ -326,8 +326,8 @@ def main():
     from paper_1504_01883_gb300 import autotune
     fixed = None
     if args.tune:
-        c, sp, mc = (int(v) for v in args.tune.split(","))
-        fixed = autotune.Tuning(lbp_ctas_per_sm=c, tc_splits=sp, tc_multicast=mc)
+        c, sp, pairing = (int(v) for v in args.tune.split(","))
+        fixed = autotune.Tuning(lbp_ctas_per_sm=c, tc_splits=sp, tc_pairing=pairing)
         fixed.apply(ctx)
 
     def stage1():
@@ -519,7 +519,7 @@ def main():
              "achieved": round(k2_tflops, 1), "peak": round(peak_t, 1) if peak_t else None, "unit": "TFLOP/s",
              "frac": round(k2_tflops / peak_t, 4) if peak_t else None,
              "traffic": measured_traffic("k2", f"splits{tuning.tc_splits}/"
-                                               f"{autotune.PAIRING_NAMES.get(tuning.tc_multicast, 'auto')}/{dt}"),
+                                               f"{autotune.PAIRING_NAMES.get(tuning.tc_pairing, 'auto')}/{dt}"),
              "algorithmic_flops": k2_flops, "ms": round(k2_ms, 4), "peak_source": src}
     dominant = rl_k2 if k2_ms >= k1_ms else rl_k1
     roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}

@@ -125,14 +125,14 @@ int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear);
  * path; scores change within rounding (the split of the SV sum).
  *   RGBD_TUNE_LBP_CTAS_PER_SM   resident fused-kernel CTAs per SM (1 or 2)
  *   RGBD_TUNE_TC_SPLITS         SV-tile ranges per 128-row block in tensor-core scoring
- *   RGBD_TUNE_TC_MULTICAST      CTA pairing of 128-row blocks in tensor-core scoring:
- *                               0 = default (3), 1 = pairs share SV tiles by TMA multicast,
- *                               2 = no pairing, 3 = each pair runs one 256-row MMA
- *                               (tcgen05 cta_group::2, each CTA holding half of the SV tile)
- * Errors: RGBD_ERR_ARG for an unknown key or a negative value. */
+ *   RGBD_TUNE_TC_PAIRING        CTA pairing of 128-row blocks in tensor-core scoring:
+ *                               0 = default (3), 2 = no pairing, 3 = each pair runs one
+ *                               256-row MMA (tcgen05 cta_group::2, each CTA holding half of
+ *                               the SV tile)
+ * Errors: RGBD_ERR_ARG for an unknown key, a negative value or a pairing other than 0, 2, 3. */
 #define RGBD_TUNE_LBP_CTAS_PER_SM 1
 #define RGBD_TUNE_TC_SPLITS 2
-#define RGBD_TUNE_TC_MULTICAST 3
+#define RGBD_TUNE_TC_PAIRING 3
 int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value);
 
 /* ======================================================================================= */
@@ -358,16 +358,18 @@ int rgbd_track_streams(rgbd_ctx* ctx, rgbd_rect* state_rects, int32_t* state_ids
 /* svm_score for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant of the RBF scoring above.
  *
- * svm_score may grow the context workspace with cudaMalloc.  Code that
- * enqueues work while a stream is being captured into a CUDA graph, real-time
- * loops that must not meet the device-wide synchronisation of cudaMalloc /
- * cudaFree, and processes whose device memory is already handed out by another
- * allocator cannot allow that.  This call allocates nothing: its partial sums
- * live in one file-scope device array of RGBD_NOALLOC_SCRATCH_BYTES that every
- * GPU loading the library holds until the process exits.
- *   - Arguments and results as in svm_score.  Only RBF models packed as
- *     RGBD_DT_BF16, RGBD_DT_FP8 or RGBD_DT_TF32 (the tensor-core path);
- *     others give RGBD_ERR_UNSUPPORTED.
+ * svm_score may grow the context workspace with cudaMalloc.  Some callers
+ * cannot allow that: real-time loops that must not meet the device-wide
+ * synchronisation that cudaMalloc / cudaFree can cause in the middle of a
+ * frame, and processes whose device memory is already handed out by another
+ * allocator (a framework's pool, a fixed budget per tenant), where a
+ * library-side cudaMalloc can fail or steal memory that was promised
+ * elsewhere.  This call allocates nothing: its partial sums live in one
+ * file-scope device array of RGBD_NOALLOC_SCRATCH_BYTES that every GPU loading
+ * the library holds until the process exits.
+ *   - Arguments and results as in svm_score.  Only RBF models packed for the
+ *     tensor-core path (RGBD_DT_BF16, RGBD_DT_BF16X3, RGBD_DT_FP8 or
+ *     RGBD_DT_TF32); others give RGBD_ERR_UNSUPPORTED.
  *   - The scratch needed grows with n x classes (4 x n x C_pad bytes per SV
  *     split plus small terms); a call that would need more than
  *     RGBD_NOALLOC_SCRATCH_BYTES launches nothing and returns RGBD_ERR_ARG with

@@ -7,8 +7,8 @@ candidate settings of the context's tuning knobs and keeps the fastest:
       128 x 128 crop laid out as 16 x 16 cells of 8 x 8 pixels, two half-cell column tiles per
       cell, so this picks between one or two such crop tiles in flight per SM;
   K2  how many SV-tile ranges ("splits") each 128-row block of the tensor-core scoring
-      kernel is cut into (the row x SV tiling across SMs), and whether CTA pairs share SV
-      tiles by TMA multicast.
+      kernel is cut into (the row x SV tiling across SMs), and whether CTA pairs run one
+      256-row MMA (tcgen05 cta_group::2) or every CTA runs its own 128-row MMA.
 
 Choices never change the integer features, only the order of the SV sum (scores move within
 rounding).  Results are cached in a JSON file keyed by GPU name and workload shape.
@@ -24,6 +24,7 @@ import torch
 
 from . import binding as B
 
+CACHE_VERSION = 2  # bumped whenever the set of knobs changes
 CACHE_PATH = os.environ.get("RGBD_TUNE_CACHE",
                             os.path.join(os.path.expanduser("~"), ".cache", "rgbd_lbp_gb300", "tune.json"))
 
@@ -32,15 +33,15 @@ CACHE_PATH = os.environ.get("RGBD_TUNE_CACHE",
 class Tuning:
     lbp_ctas_per_sm: int = 0
     tc_splits: int = 0
-    tc_multicast: int = 0
+    tc_pairing: int = 0
 
     def apply(self, ctx):
         ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, self.lbp_ctas_per_sm)
         ctx.set_tuning(B.TUNE_TC_SPLITS, self.tc_splits)
-        ctx.set_tuning(B.TUNE_TC_MULTICAST, self.tc_multicast)
+        ctx.set_tuning(B.TUNE_TC_PAIRING, self.tc_pairing)
 
 
-PAIRING_NAMES = {1: "mc", 2: "single", 3: "pair"}
+PAIRING_NAMES = {2: "single", 3: "pair"}
 
 
 def _time(fn, stream, reps=3):
@@ -92,12 +93,16 @@ def tune(ctx, key, stage1, stage2, n_rows, n_sv, stream, use_cache=True, tensor_
     """Pick the fastest Tuning for the workload `key` (stage1 / stage2 enqueue the two stages
     on `stream`).  Returns (tuning, report)."""
     dev = torch.cuda.get_device_name()
-    full_key = f"{dev}|{key}"
+    full_key = f"{dev}|{CACHE_VERSION}|{key}"
     cache = _load_cache() if use_cache else {}
     if full_key in cache:
-        t = Tuning(**cache[full_key]["tuning"])
-        t.apply(ctx)
-        return t, dict(cache[full_key], cached=True)
+        try:
+            t = Tuning(**cache[full_key]["tuning"])
+        except TypeError:
+            t = None  # an entry written by another version of the knobs
+        if t is not None:
+            t.apply(ctx)
+            return t, dict(cache[full_key], cached=True)
     report = {"k1": {}, "k2": {}}
     best = Tuning()
     # K1: CTAs per SM
@@ -113,13 +118,13 @@ def tune(ctx, key, stage1, stage2, n_rows, n_sv, stream, use_cache=True, tensor_
     if tensor_core:
         best_ms = None
         for sp in split_candidates(n_rows, n_sv, torch.cuda.get_device_properties(0).multi_processor_count):
-            for mc in (3, 1, 2):
+            for pairing in (3, 2):
                 ctx.set_tuning(B.TUNE_TC_SPLITS, sp)
-                ctx.set_tuning(B.TUNE_TC_MULTICAST, mc)
+                ctx.set_tuning(B.TUNE_TC_PAIRING, pairing)
                 ms = _time(stage2, stream)
-                report["k2"][f"{sp}/{PAIRING_NAMES[mc]}"] = ms
+                report["k2"][f"{sp}/{PAIRING_NAMES[pairing]}"] = ms
                 if best_ms is None or ms < best_ms:
-                    best_ms, best.tc_splits, best.tc_multicast = ms, sp, mc
+                    best_ms, best.tc_splits, best.tc_pairing = ms, sp, pairing
     best.apply(ctx)
     entry = {"tuning": asdict(best), "report": report}
     cache[full_key] = entry

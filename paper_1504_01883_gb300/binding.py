@@ -23,7 +23,7 @@ RGBD_OK = 0
 DT_F32, DT_BF16, DT_FP8, DT_TF32, DT_BF16X3 = 1, 2, 3, 4, 5
 KERNEL_LINEAR, KERNEL_RBF = 0, 1
 LBP_GE, LBP_NBR_IGNORE_MASK, LBP_FACE_HIST256 = 1, 2, 4
-TUNE_LBP_CTAS_PER_SM, TUNE_TC_SPLITS, TUNE_TC_MULTICAST = 1, 2, 3
+TUNE_LBP_CTAS_PER_SM, TUNE_TC_SPLITS, TUNE_TC_PAIRING = 1, 2, 3
 STATUS_BAD_RECT, STATUS_WAIT_TIMEOUT = 1, 2
 NBINS, CELL = 59, 8
 
@@ -387,9 +387,9 @@ def svm_score(ctx, model, x, xsq=None, x_scale=448.0, scores=None, labels=None, 
 def svm_score_noalloc(ctx, model, x, xsq, x_scale=448.0, scores=None, labels=None, want_labels=True, stream=None):
     """svm_score without any device allocation inside the call (see include/rgbd_lbp.h).
 
-    For callers that cannot let the library call cudaMalloc (work enqueued during CUDA-graph
-    capture, real-time loops, processes whose device memory another allocator owns): the
-    partial sums live in the library's fixed 16 MiB per-GPU scratch array.  Output tensors
+    For callers that cannot let the library call cudaMalloc (real-time loops that must not
+    meet its device-wide synchronisation, processes whose device memory another allocator
+    owns): the partial sums live in the library's fixed 16 MiB per-GPU scratch array.  Output tensors
     are allocated here only when the caller does not pass them.  Calls that overlap on the GPU
     share that array and race; keep them on one stream.
     """

@@ -147,9 +147,9 @@ int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value) {
         case RGBD_TUNE_TC_SPLITS:
             ctx->tune_tc_splits = value;
             return RGBD_OK;
-        case RGBD_TUNE_TC_MULTICAST:
-            CHECK_ARG(value <= 3, "rgbd_ctx_set_tuning: CTA pairing %d (0, 1, 2 or 3)", value);
-            ctx->tune_tc_multicast = value;
+        case RGBD_TUNE_TC_PAIRING:
+            CHECK_ARG(value == 0 || value == 2 || value == 3, "rgbd_ctx_set_tuning: CTA pairing %d (0, 2 or 3)", value);
+            ctx->tune_tc_pairing = value;
             return RGBD_OK;
         default:
             return set_error(RGBD_ERR_ARG, "rgbd_ctx_set_tuning: unknown key %d", key);

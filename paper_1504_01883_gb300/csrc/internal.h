@@ -42,7 +42,7 @@ struct rgbd_ctx {
     rgbd::DeviceProps props;
     int tune_lbp_ctas_per_sm = 0;  // 0 = occupancy limit
     int tune_tc_splits = 0;        // 0 = cost model
-    int tune_tc_multicast = 0;     // CTA pairing: 0 = auto, 1 = multicast, 2 = none, 3 = 2-CTA MMA
+    int tune_tc_pairing = 0;       // CTA pairing: 0 = auto, 2 = none, 3 = 2-CTA MMA pairs
     uint32_t* d_status = nullptr;  // device status word, followed by kFaceCounters face-queue counters
     uint32_t* d_counters = nullptr;
     uint32_t counter_next = 0;     // next counter of the pool (a launch takes one and zeroes it)
@@ -68,7 +68,7 @@ struct rgbd_svm {
     float* asum_tile = nullptr;  // RBF: [n_pad / kSvTile][C_pad] sum of a_ci over each SV tile (fp64)
     float* bias = nullptr;    // [C]
     CUtensorMap tm_sv;        // tensor-core path: TMA descriptors (a whole SV tile, ...
-    CUtensorMap tm_sv_half;   // ... half of it, for the multicast of a CTA pair)
+    CUtensorMap tm_sv_half;   // ... half of it, the share of each CTA of a 2-CTA MMA pair)
     CUtensorMap tm_sv_lo;     // RGBD_DT_BF16X3: the same two maps over the lo plane
     CUtensorMap tm_sv_lo_half;
     CUtensorMap tm_coef;

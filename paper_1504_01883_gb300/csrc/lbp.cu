@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
     }
     // Quotient table of the bf16 output: a cell has at most 64 centres, so every normalised value
     // is one of the 65 x 65 quotients h / n, computed once per CTA exactly as the other output
-    // types compute them (IEEE single quotient, then round to nearest even bf16).  Entry
+    // types compute them (IEEE single quotient by the reciprocal and Markstein's one-fma
+    // correction, then round to nearest even bf16).  Entry
     // 128 n + h, so that a staged count with its cell's centre count above it is the index.
     for (int i = tid; i < 65 * 128; i += NT) {
         const int n = i >> 7, hh = min(i & 127, 64);
@@ -699,8 +700,10 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 *reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(a.x_out) + (size_t)face * a.k_pad + j) =
                     make_uint2(pk[0], pk[1]);
             } else if (x_dtype) {
-                // x = h / n as the IEEE single quotient: q0 = h * (1/n), then one fma correction.
-                // For 0 <= h <= n <= 64 (a cell has 64 pixels) this reproduces div.rn exactly
+                // x = h / n as the IEEE single quotient: q0 = h * (1/n), then Markstein's
+                // correction step (P. Markstein, IBM J. Res. Dev. 34(1), 1990): the remainder
+                // r = h - q0 n exactly by one fma, then q = q0 + r (1/n) rounded once.  For
+                // 0 <= h <= n <= 64 (a cell has 64 pixels) this reproduces div.rn exactly
                 // (checked exhaustively); an empty cell has h = 0 and rcp = 0, giving 0.
                 float x[4] = {0.f, 0.f, 0.f, 0.f};
                 if (j < DIM) {  // DIM is a multiple of 4, so the whole group is inside

@@ -1,12 +1,11 @@
 // noalloc.cu -- svm_score_noalloc: RBF scoring on the tensor cores that allocates no device memory.
 //
 // svm_score keeps its partial sums in the context workspace, which it grows with cudaMalloc
-// when a call needs more.  Some callers cannot allow that: code that enqueues work while a
-// stream is being captured into a CUDA graph (a capture must not allocate), real-time loops
-// that cannot afford the device-wide synchronisation that cudaMalloc / cudaFree may cause,
-// and processes whose free device memory is already owned by another allocator.  This entry
-// point keeps its scratch in one fixed-size array of device memory that belongs to the
-// library's module instead.
+// when a call needs more.  Some callers cannot allow that: real-time loops that cannot afford
+// the device-wide synchronisation that cudaMalloc / cudaFree may cause in the middle of a
+// frame, and processes whose free device memory is already owned by another allocator (a
+// framework's pool, a fixed per-tenant budget).  This entry point keeps its scratch in one
+// fixed-size array of device memory that belongs to the library's module instead.
 #include <mutex>
 
 #include "internal.h"
@@ -48,7 +47,7 @@ extern "C" int svm_score_noalloc(rgbd_ctx* ctx, const rgbd_svm* model, const voi
     if (!model->scorable) return set_error(RGBD_ERR_ARG, "svm_score_noalloc: model was packed without coefficients");
     if (model->kernel != RGBD_KERNEL_RBF || model->dtype == RGBD_DT_F32)
         return set_error(RGBD_ERR_UNSUPPORTED,
-                         "svm_score_noalloc: only RBF models packed as BF16, FP8 or TF32 (tensor-core path)");
+                         "svm_score_noalloc: only RBF models packed as BF16, BF16X3, FP8 or TF32 (tensor-core path)");
     if (n < 0) return set_error(RGBD_ERR_ARG, "svm_score_noalloc: n %d < 0", n);
     if (n == 0) return RGBD_OK;
     if (!x || !xsq || !scores) return set_error(RGBD_ERR_ARG, "svm_score_noalloc: NULL x, xsq or scores");

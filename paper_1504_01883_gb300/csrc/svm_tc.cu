@@ -46,8 +46,7 @@ constexpr int MAX_STAGES = 6;
 
 // Launch modes of the kernel.
 enum { MODE_SINGLE = 0,   // one CTA per (row block, split)
-       MODE_MC = 1,       // CTA pairs; each loads half of every SV k-block and multicasts it
-       MODE_PAIR = 2 };   // CTA pairs run one 256-row MMA (cta_group::2): each CTA holds its own
+       MODE_PAIR = 1 };   // CTA pairs run one 256-row MMA (cta_group::2): each CTA holds its own
                           // 128 X rows and half of the SV tile (and of the coefficient chunk)
 
 // Shared-memory layout of a mode: main ring, coefficient ring (2 slots), barriers.  (The F
@@ -210,22 +209,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
-// TMA load multicast to the CTAs of `mask` in the cluster: same CTA-relative destination offset
-// and mbarrier in each of them.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-        "h"(mask)
-        : "memory");
-}
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -257,7 +240,8 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap
 __device__ __forceinline__ void tc_commit2(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tc_commit2_mc(uint32_t bar, uint16_t mask) {
+// Commit of a 2-CTA MMA pair whose arrive lands on the same barrier in both CTAs of `mask`.
+__device__ __forceinline__ void tc_commit2_pair(uint32_t bar, uint16_t mask) {
     asm volatile(
         "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
         "h"(mask)
@@ -358,9 +342,6 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 // ---------------------------------------------------------------------------------------
 // The kernel
 // ---------------------------------------------------------------------------------------
-// MODE_MC: the CTA runs in a cluster of two along the rows.  Both CTAs use the same SV tiles, so
-// each loads half of every SV k-block and multicasts it into both CTAs' stage, and each CTA's MMA
-// releases the stage in both CTAs: the pair reads each SV k-block from L2 once.
 // MODE_PAIR: the two CTAs of a cluster form one 256-row MMA (tcgen05 cta_group::2).  Each CTA
 // loads its own 128 X rows and one half of the SV tile (CTA r: SVs r*128 .. r*128+127 of the
 // tile) and one half of the classes of each coefficient chunk; CTA 0 issues every MMA, which
@@ -373,13 +354,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                   const __grid_constant__ CUtensorMap tm_coef, const __grid_constant__ CUtensorMap tm_x2,
                   const __grid_constant__ CUtensorMap tm_sv2, const __grid_constant__ CUtensorMap tm_coef2,
                   const TcParams p) {
-    constexpr bool MC = MODE == MODE_MC, PAIR = MODE == MODE_PAIR;
+    constexpr bool PAIR = MODE == MODE_PAIR;
     constexpr bool SPLIT2 = KIND == 3;
     constexpr int CG = PAIR ? 2 : 1;
     constexpr uint32_t F_SLOT = SPLIT2 ? 64u : 32u;  // TMEM columns per F slot
     using L = Lay<MODE, SPLIT2>;
     // Pairs fill and release ring stages two at a time (one FULL and one EMPTY barrier per
-    // group): a 2-CTA multicast commit per k-block cost ~5 % of the kernel (the ring turned over
+    // group): a 2-CTA commit per k-block cost ~5 % of the kernel (the ring turned over
     // slower than its copies land).  Single CTAs, with a 4-stage ring, keep one per stage.
     constexpr int GRP = (MODE == MODE_PAIR && L::STAGES % 2 == 0) ? 2 : 1;  // stages released per commit
     extern __shared__ unsigned char smem_raw[];
@@ -402,7 +383,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < L::STAGES; ++s) {
             bar_init(bar(B_FULL + s), 1);
-            bar_init(bar(B_EMPTY + s), MC ? 2 : 1);  // both CTAs' MMAs read a multicast stage
+            bar_init(bar(B_EMPTY + s), 1);
         }
         bar_init(bar(B_GFULL), 1);
         bar_init(bar(B_GEMPTY), PAIR ? 32 : 16);  // the epilogue warps (of both CTAs of a pair)
@@ -436,13 +417,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     tc_fence_before();
     __syncwarp();
-    if (MC || PAIR)
+    if (PAIR)
         cluster_sync();  // the peer's barriers are initialised before any copy or commit reaches them
     else
         __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t crank = (MC || PAIR) ? cluster_rank() : 0u;
+    const uint32_t crank = PAIR ? cluster_rank() : 0u;
     const uint32_t coef_chunk_bytes = (uint32_t)(PAIR ? p.C_pad / 2 : p.C_pad) * 128u;
 
     if (warp == 0) {
@@ -482,11 +463,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     } else {
                         bar_arrive_tx(bar(B_FULL + stage), L::STAGE);
                         tma_load_2d(sa, mx, kb * p.k_elems, m0, bar(B_FULL + stage));
-                        if (MC)
-                            tma_load_2d_mc(sa + X_TILE + crank * (SV_TILE / 2), msv, kb * p.k_elems,
-                                           n0 + (int)crank * (BN / 2), bar(B_FULL + stage), (uint16_t)0x3);
-                        else
-                            tma_load_2d(sa + X_TILE, msv, kb * p.k_elems, n0, bar(B_FULL + stage));
+                        tma_load_2d(sa + X_TILE, msv, kb * p.k_elems, n0, bar(B_FULL + stage));
                     }
                     armed |= 1u << stage;
                     armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
@@ -575,7 +552,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                 }
                 if (PAIR)
-                    tc_commit2_mc(bar(B_FEMPTY + slot), (uint16_t)0x3);
+                    tc_commit2_pair(bar(B_FEMPTY + slot), (uint16_t)0x3);
                 else
                     tc_commit(bar(B_FEMPTY + slot));
                 ++q_next;
@@ -628,9 +605,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     // release a group after its last stage (and after the split's last k-block)
                     if (GRP == 1 || stage % GRP == GRP - 1 || (u == U - 1 && kt == p.passes * p.k_blocks - 1)) {
                         if (PAIR)
-                            tc_commit2_mc(bar(B_EMPTY + stage / GRP), (uint16_t)0x3);
-                        else if (MC)
-                            tc_commit_mc(bar(B_EMPTY + stage / GRP), (uint16_t)0x3);
+                            tc_commit2_pair(bar(B_EMPTY + stage / GRP), (uint16_t)0x3);
                         else
                             tc_commit(bar(B_EMPTY + stage / GRP));
                     }
@@ -642,7 +617,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 }
                 if (!alive) break;
                 if (PAIR)
-                    tc_commit2_mc(bar(B_GFULL), (uint16_t)0x3);
+                    tc_commit2_pair(bar(B_GFULL), (uint16_t)0x3);
                 else
                     tc_commit(bar(B_GFULL));
                 q_avail = 4 * (u + 1);
@@ -661,7 +636,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
             if (alive) {
                 if (PAIR)
-                    tc_commit2_mc(bar(B_DFULL), (uint16_t)0x3);
+                    tc_commit2_pair(bar(B_DFULL), (uint16_t)0x3);
                 else
                     tc_commit(bar(B_DFULL));
             }
@@ -816,8 +791,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
     tc_fence_before();
     __syncwarp();
-    if (MC || PAIR)
-        cluster_sync();  // no CTA leaves while its peer may still multicast into it or arrive on it
+    if (PAIR)
+        cluster_sync();  // no CTA leaves while its peer's commits may still arrive on it
     else
         __syncthreads();
     if (warp == 1) {
@@ -1004,13 +979,10 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     rc = encode_tmap_2d(&tm_x2, pl.dt, x_lo, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * pl.esz,
                         128u / pl.esz, BM, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
-    // Mode: tuning value 1 = multicast pairs, 2 = single CTAs, 3 = 2-CTA MMA pairs, 0 = auto (the
-    // 2-CTA pairs).  Pairs need at least two 128-row blocks.
+    // Mode: tuning value 2 = single CTAs, 3 = 2-CTA MMA pairs, 0 = auto (the 2-CTA pairs).
+    // Pairs need at least two 128-row blocks.
     int mode = MODE_SINGLE;
-    if (pl.mt >= 2) {
-        const int t = ctx->tune_tc_multicast;
-        mode = (t == 1) ? MODE_MC : (t == 2) ? MODE_SINGLE : MODE_PAIR;
-    }
+    if (pl.mt >= 2) mode = (ctx->tune_tc_pairing == 2) ? MODE_SINGLE : MODE_PAIR;
     TcParams p;
     p.n = n;
     p.n_sv = m->n_sv;
@@ -1037,10 +1009,6 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
         case MODE_SINGLE * 4 + 1: e = launch_mode<MODE_SINGLE, 1>(pl, p, m, tm_x, tm_x2, s); break;
         case MODE_SINGLE * 4 + 2: e = launch_mode<MODE_SINGLE, 2>(pl, p, m, tm_x, tm_x2, s); break;
         case MODE_SINGLE * 4 + 3: e = launch_mode<MODE_SINGLE, 3>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_MC * 4 + 0: e = launch_mode<MODE_MC, 0>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_MC * 4 + 1: e = launch_mode<MODE_MC, 1>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_MC * 4 + 2: e = launch_mode<MODE_MC, 2>(pl, p, m, tm_x, tm_x2, s); break;
-        case MODE_MC * 4 + 3: e = launch_mode<MODE_MC, 3>(pl, p, m, tm_x, tm_x2, s); break;
         case MODE_PAIR * 4 + 0: e = launch_mode<MODE_PAIR, 0>(pl, p, m, tm_x, tm_x2, s); break;
         case MODE_PAIR * 4 + 1: e = launch_mode<MODE_PAIR, 1>(pl, p, m, tm_x, tm_x2, s); break;
         case MODE_PAIR * 4 + 2: e = launch_mode<MODE_PAIR, 2>(pl, p, m, tm_x, tm_x2, s); break;

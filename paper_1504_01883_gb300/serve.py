@@ -3,7 +3,8 @@
 Frames from many cameras arrive at Poisson times.  The loop keeps the packed SVM model and a
 pool of frame slots resident on the GPU and runs, on one compute stream, batches of all faces
 of all frames that have been uploaded.  While a batch runs, frames that arrive meanwhile are
-admitted (when a slot is free and the device has memory to spare) and uploaded on a separate
+admitted (when a slot is free, the frame's bytes fit the server's device-memory budget and the
+device has memory to spare) and uploaded on a separate
 copy stream, so they form the next batch as soon as the GPU frees up: uploads overlap compute
 and batches follow each other with no gap.  Every frame's latency is measured from its arrival
 to the moment its scores and labels are on the host.
@@ -65,24 +66,43 @@ class FrameRequest:
 
 
 class MemoryAdmission:
-    """Admits a frame when a slot is free and the device keeps `reserve_bytes` free."""
+    """Admits a frame when a frame slot is free, the frame's device bytes fit the server's
+    device-memory budget, and the device keeps `reserve_bytes` free for everyone else.
 
-    def __init__(self, n_slots, reserve_bytes=256 << 20, mem_get_info=None):
+    A frame charges its upload (the grey and depth planes) plus, per face, the device rows its
+    faces occupy until the frame is done (normalised feature row, norm, scores, label, identity,
+    rect).  The charge is returned when the frame's results are on the host.  The server's
+    buffers are allocated up front, so `budget_bytes` is the size of the part of them that
+    frames draw on; the slot count bounds the frames in flight, the budget bounds their bytes
+    (frames with many faces take more of it), and the free-memory check reacts to other users of
+    the device.  Without a budget only the slots and the reserve apply."""
+
+    def __init__(self, n_slots, reserve_bytes=256 << 20, mem_get_info=None, budget_bytes=None):
         self.free_slots = collections.deque(range(n_slots))
         self.reserve = reserve_bytes
         self.mem_get_info = mem_get_info or torch.cuda.mem_get_info
+        self.budget = budget_bytes
+        self.used = 0
+        self.charged = {}
         self.rejections = 0
 
-    def try_admit(self):
+    def try_admit(self, nbytes=0):
         if not self.free_slots:
+            return -1
+        if self.budget is not None and self.used + nbytes > self.budget:
+            self.rejections += 1
             return -1
         free, _ = self.mem_get_info()
         if free < self.reserve:
             self.rejections += 1
             return -1
-        return self.free_slots.popleft()
+        slot = self.free_slots.popleft()
+        self.used += nbytes
+        self.charged[slot] = nbytes
+        return slot
 
     def release(self, slot):
+        self.used -= self.charged.pop(slot, 0)
         self.free_slots.append(slot)
 
 
@@ -156,7 +176,13 @@ class BatchServer:
             })
         self.compute = torch.cuda.Stream(device=self.dev)
         self.copy = torch.cuda.Stream(device=self.dev)
-        self.admission = admission or MemoryAdmission(n_slots)
+        # device bytes a frame holds while it is in flight: its planes, and per face the rows
+        # of the batch buffers (normalised row, norm, scores, label, identity, rect)
+        self.frame_bytes = H * W * 3
+        self.face_bytes = (self.bufs[0]["x"][0].numel() * self.bufs[0]["x"].element_size() + 4 + 4 * C + 4 + 4
+                           + 20)
+        budget = n_slots * self.frame_bytes + 2 * max_faces * self.face_bytes
+        self.admission = admission or MemoryAdmission(n_slots, budget_bytes=budget)
         self.slot_ready = {}   # slot -> event recorded after its upload
         # per-stream state kept on the device: the faces of each stream's last served frame and
         # their identities (Section 2.3 tracking), updated by every batch in arrival order
@@ -166,6 +192,10 @@ class BatchServer:
         s = self.streams[req.stream]
         k = req.index % len(s.rects)
         return k, s.rects[k]
+
+    def _bytes(self, req):
+        """Device bytes the request holds until its results are on the host."""
+        return self.frame_bytes + len(self._frame(req)[1]) * self.face_bytes
 
     def _upload(self, req):
         k, rects = self._frame(req)
@@ -232,7 +262,7 @@ class BatchServer:
     def serve_one(self, stream, index):
         """Serves frame `index` of `stream` alone (a batch of one frame); returns the request."""
         req = FrameRequest(0.0, int(stream), int(index))
-        req.slot = self.admission.try_admit()
+        req.slot = self.admission.try_admit(self._bytes(req))
         if req.slot < 0:
             raise RuntimeError("no free frame slot")
         self._upload(req)
@@ -264,7 +294,7 @@ class BatchServer:
             while pending and pending[0].t_arrival <= now:
                 waiting.append(pending.popleft())
             while waiting:
-                slot = self.admission.try_admit()
+                slot = self.admission.try_admit(self._bytes(waiting[0]))
                 if slot < 0:
                     break
                 req = waiting.popleft()

@@ -21,6 +21,20 @@ def test_admission_waits_for_memory_and_slots():
     assert adm.try_admit() == a
 
 
+def test_admission_charges_each_frames_bytes_against_the_budget():
+    pytest.importorskip("torch")
+    from paper_1504_01883_gb300.serve import MemoryAdmission
+    adm = MemoryAdmission(4, reserve_bytes=0, mem_get_info=lambda: (1 << 40, 1 << 40), budget_bytes=1000)
+    a = adm.try_admit(600)
+    assert a >= 0 and adm.used == 600
+    assert adm.try_admit(500) == -1 and adm.rejections == 1   # a slot is free, the bytes are not
+    b = adm.try_admit(400)
+    assert b >= 0 and adm.used == 1000
+    adm.release(a)
+    assert adm.used == 400
+    assert adm.try_admit(500) >= 0 and adm.used == 900
+
+
 def test_arrivals_are_seeded_and_ordered():
     ev = synth.serving_arrivals(seed=3, n_streams=4, seconds=1.0)
     assert ev == sorted(ev)
