@@ -279,6 +279,8 @@ def main():
     ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision", "roi", "train"],
                     help="batch: the headline line; the others measure the remaining workloads")
     ap.add_argument("--seconds", type=float, default=10.0, help="serving: simulated seconds of arrivals")
+    ap.add_argument("--serving-seconds", type=float, default=3.0,
+                    help="batch line: simulated seconds of the serving leg (0: leave it out)")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -540,6 +542,11 @@ def main():
     line["config"]["schedule"] = ("sequential steps" if args.no_overlap else
                                   "two streams, double-buffered outputs: step i+1's feature kernel runs on the SMs "
                                   "that step i's scoring leaves idle; stage durations from a sequential pass")
+    if world == 1 and args.serving_seconds > 0:
+        # p50 / p99 frame latency of the serving workload, batched against per-crop (not part
+        # of the timed steps above)
+        import bench_workloads
+        line["serving"] = bench_workloads.serving_leg(ctx, args.serving_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         one = cpu_baseline(wl)
         try:

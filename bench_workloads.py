@@ -272,12 +272,14 @@ def run_precision(args):
 
 
 # ---------------------------------------------------------------------------------------------
-def run_serving(args):
+def serving_leg(ctx, seconds, warm_frames=50):
+    """Serving workload: 32 Poisson camera streams at 30 fps against a resident 8192-SV model,
+    served by the continuous-batching loop and by the plain per-crop path.  Latency of a frame:
+    from its arrival to its scores and labels in host memory (upload, features, scoring and
+    read-back included).  Returns the summaries of both paths."""
     import torch
-    from paper_1504_01883_gb300 import _build, serve, synth
+    from paper_1504_01883_gb300 import serve, synth
     from paper_1504_01883_gb300 import binding as B
-    _build.build()
-    ctx = B.Context(0)
     dev = torch.device("cuda")
     dim = 16 * 16 * 59
     rng = synth.rng_for(1508 + 5)
@@ -286,20 +288,31 @@ def run_serving(args):
     model = B.svm_train_data_pack(ctx, torch.from_numpy(sv.view(np.int16)).to(dev), torch.from_numpy(a).to(dev),
                                   torch.from_numpy(b).to(dev), gamma=1.0 / dim, dtype="bf16")
     streams = serve.make_streams()
-    events = synth.serving_arrivals(seconds=args.seconds)
-    out = {}
+    events = synth.serving_arrivals(seconds=seconds)
+    out = {"workload": f"serving: 32 RGB-D streams x 30 fps (Poisson arrivals, {seconds:g} s), 640x480, "
+                       "1-12 faces per frame, sides U{48..256} -> 128x128, RBF 8192 SVs (BF16) x 64 classes "
+                       "resident",
+           "latency": "arrival of the frame -> its scores and labels in host memory",
+           "frames": len(events), "offered_crops_per_s": sum(k for _, _, k in events) / seconds}
     for name, cls in [("batched", serve.BatchServer), ("per_crop", serve.PerCropServer)]:
         srv = cls(ctx, model, streams)
-        srv.run(events[:50], realtime=False)  # warm-up
+        srv.run(events[:warm_frames], realtime=False)  # warm-up
         rep, _ = srv.run(events, realtime=True)
-        out[name] = rep.summary()
+        out[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.summary().items()}
         del srv
         torch.cuda.empty_cache()
-    demand = sum(len(streams[s].rects[0]) for s in range(len(streams)))  # noqa: F841 (kept for clarity)
-    return _emit({"workload": f"serving: 32 RGB-D streams x 30 fps (Poisson arrivals, {args.seconds:.0f} s), 640x480, "
-                              "1-12 faces per frame, sides U{48..256} -> 128x128, RBF 8192 SVs (BF16) x 64 classes "
-                              "resident", "metric": "p50/p99 frame latency (ms) and crops/s",
-                  "frames": len(events), "batched": out["batched"], "per_crop": out["per_crop"]})
+    model.free()
+    return out
+
+
+def run_serving(args):
+    from paper_1504_01883_gb300 import _build
+    from paper_1504_01883_gb300 import binding as B
+    _build.build()
+    ctx = B.Context(0)
+    out = serving_leg(ctx, args.seconds)
+    out["metric"] = "p50/p99 frame latency (ms) and crops/s"
+    return _emit(out)
 
 
 def run_roi(args):
