@@ -45,7 +45,7 @@ X_ELEM = {"f32": 4, "tf32": 4, "bf16": 2, "fp8": 1, "bf16x3": 4}
 # digest covers the source with comments and blank space removed, so only a code change (or a
 # changed layout) reports null.
 MEASURED_TRAFFIC = {
-    "k1": ("lbp.cu", "459f85c0e40ffc70", "ctas2/bf16", 189_343_488 + 197_043_968),
+    "k1": ("lbp.cu", "459f85c0e40ffc70", "shape2/ctas2/bf16", 189_343_488 + 197_043_968),
     "k2": ("svm_tc.cu", "9583ef37d017e276", "splits4/pair/bf16", 617_098_496 + 4_231_168),
 }
 
@@ -272,9 +272,10 @@ def main():
     ap.add_argument("--no-overlap", action="store_true",
                     help="run the timed steps strictly one after the other (by default step i+1's feature "
                          "kernel overlaps step i's scoring)")
-    ap.add_argument("--tune", default=None, metavar="CTAS,SPLITS,PAIRING",
+    ap.add_argument("--tune", default=None, metavar="CTAS,SPLITS,PAIRING[,SHAPE]",
                     help="fixed launch layout (K1 CTAs/SM, scoring splits, CTA pairing 2=none "
-                         "3=2-CTA MMA) instead of the autotuner, e.g. to profile the layout a previous run chose")
+                         "3=2-CTA MMA, K1 threads per cell 2 or 1) instead of the autotuner, e.g. to profile "
+                         "the layout a previous run chose")
     ap.add_argument("--ref-crops-per-step", type=int, default=8)
     ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision", "roi", "train"],
                     help="batch: the headline line; the others measure the remaining workloads")
@@ -328,8 +329,10 @@ def main():
     from paper_1504_01883_gb300 import autotune
     fixed = None
     if args.tune:
-        c, sp, pairing = (int(v) for v in args.tune.split(","))
-        fixed = autotune.Tuning(lbp_ctas_per_sm=c, tc_splits=sp, tc_pairing=pairing)
+        vals = [int(v) for v in args.tune.split(",")]
+        c, sp, pairing = vals[:3]
+        shape = vals[3] if len(vals) > 3 else 2
+        fixed = autotune.Tuning(lbp_ctas_per_sm=c, tc_splits=sp, tc_pairing=pairing, lbp_shape=shape)
         fixed.apply(ctx)
 
     def stage1():
@@ -513,9 +516,9 @@ def main():
         peak_t = None
     else:
         peak_t = pk["bf16_tflops"] * NOMINAL_RATIO[dt]
-    rl_k1 = {"kernel": "lbp_fused_kernel<128>", "bound": "hbm", "achieved": round(k1_gbs, 1),
+    rl_k1 = {"kernel": f"lbp_fused_kernel<128, {tuning.lbp_shape or 2}>", "bound": "hbm", "achieved": round(k1_gbs, 1),
              "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(k1_gbs / pk["hbm_gbs"], 4),
-             "traffic": measured_traffic("k1", f"ctas{tuning.lbp_ctas_per_sm}/{dt}"),
+             "traffic": measured_traffic("k1", f"shape{tuning.lbp_shape or 2}/ctas{tuning.lbp_ctas_per_sm}/{dt}"),
              "algorithmic_bytes": k1_bytes, "ms": round(k1_ms, 4), "peak_source": src}
     rl_k2 = {"kernel": "rbf_tc_kernel" if dt != "f32" else "rbf_tiled_kernel", "bound": "tensor" if peak_t else "alu",
              "achieved": round(k2_tflops, 1), "peak": round(peak_t, 1) if peak_t else None, "unit": "TFLOP/s",
@@ -546,7 +549,9 @@ def main():
         # p50 / p99 frame latency of the serving workload, batched against per-crop (not part
         # of the timed steps above)
         import bench_workloads
-        line["serving"] = bench_workloads.serving_leg(ctx, args.serving_seconds)
+        sctx = B.Context(dev.index or 0)  # its own context: the batch tuning above fits only that batch
+        line["serving"] = bench_workloads.serving_leg(sctx, args.serving_seconds)
+        sctx.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         one = cpu_baseline(wl)
         try:

@@ -196,9 +196,12 @@ def run_precision(args):
     labels = {}
     sub_scores = {}
     x_scale = 448.0
-    for dt in ["f32", "bf16", "fp8", "tf32", "bf16x3"]:
-        model = B.svm_train_data_pack(ctx, SV, at, bt, gamma=gamma, dtype=dt)
-        x, q = B.lbp_normalize_features(ctx, X, dt, x_scale=x_scale)
+    modes = [("f32", False), ("bf16", False), ("fp8", False), ("tf32", False), ("bf16x3", False),
+             ("bf16", True), ("fp8", True)]
+    for dt_base, centred in modes:
+        dt = dt_base + ("_centred" if centred else "")
+        model = B.svm_train_data_pack(ctx, SV, at, bt, gamma=gamma, dtype=dt_base, centred=centred)
+        x, q = B.lbp_normalize_features(ctx, X, dt_base, x_scale=x_scale, x_centre=model if centred else None)
         s_out, l_out = B.svm_score(ctx, model, x, q, x_scale=x_scale)
         torch.cuda.synchronize()
         reps = 1 if dt == "f32" else 3
@@ -212,7 +215,7 @@ def run_precision(args):
             ts.append(e0.elapsed_time(e1))
         ms = float(np.median(ts))
         flops = 2.0 * n_rows * n_sv * dim + 2.0 * n_rows * n_sv * C
-        ratio = {"bf16": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25, "bf16x3": 1.0 / 3.0}.get(dt)
+        ratio = {"bf16": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25, "bf16x3": 1.0 / 3.0}.get(dt_base)
         peak = pk["bf16_tflops"] * ratio if ratio else None
         res[dt] = {"ms": ms, "tflops": flops / ms / 1e9, "frac_of_peak": (flops / ms / 1e9) / peak if peak else None,
                    "peak_tflops": peak}
@@ -251,8 +254,17 @@ def run_precision(args):
     lab_big = orc.argmax(ref_big)
     sb = np.sort(ref_big, axis=1)
     margin_big = sb[:, -1] - sb[:, -2]
+    # fp64 top-1 / top-2 margins in decades, and per mode the rows whose label differs from
+    # exact fp32's in each decade: where the labels part is set by the margin, not by the mode
+    edges = [0.0] + [10.0 ** k for k in range(-9, -2)] + [np.inf]
+    names = ["<1e-9"] + [f"1e{k}..1e{k + 1}" for k in range(-9, -3)] + [">=1e-3"]
+    hist = {nm: int(((margin_big >= lo) & (margin_big < hi)).sum()) for nm, lo, hi in zip(names, edges[:-1], edges[1:])}
     for dt in res:
         err = np.abs(sub_scores[dt].astype(np.float64) - ref)
+        differs = labels[dt][:big] != labels["f32"][:big]
+        res[dt]["rows_differing_from_f32_by_fp64_margin"] = {
+            nm: int((differs & (margin_big >= lo) & (margin_big < hi)).sum())
+            for nm, lo, hi in zip(names, edges[:-1], edges[1:])}
         res[dt]["max_abs_err_vs_fp64"] = float(err.max())
         res[dt]["max_rel_err_vs_fp64"] = float((err / scale).max())
         res[dt]["label_agreement_vs_fp64_sample"] = float((labels[dt][:oracle_rows] == ref_lab).mean())
@@ -267,6 +279,7 @@ def run_precision(args):
                   "results": res, "oracle_rows": oracle_rows, "oracle_s": t_oracle,
                   "fp64_blas_rows": big, "fp64_blas_s": t_blas, "fp64_blas_vs_oracle_max_abs": blas_vs_oracle,
                   "fp64_margin_below_1e-6_fraction": float((margin_big < 1e-6).mean()),
+                  "fp64_margin_histogram_rows": hist,
                   "fp64_margin_top1_top2": {"min": float(margin.min()), "median": float(np.median(margin))},
                   "peak_source": src})
 

@@ -58,6 +58,15 @@ extern "C" {
                             to 2^-18; scored with three BF16 MMAs (hi.hi + hi.lo + lo.hi), fp32
                             accumulate.  A row buffer holds the hi plane [n][k_pad] followed by
                             the lo plane [n][k_pad]. */
+#define RGBD_DT_CENTRED 0x100 /* svm_train_data_pack flag, OR-ed into an RBF model's dtype: the
+                            support vectors are stored relative to their mean mu (a float per
+                            feature column, computed in fp64 and rounded to fp32).  The RBF
+                            kernel depends only on x - sv_i, so the scores are those of the
+                            uncentred model up to rounding, while the centred values are about
+                            half as large in magnitude and their bf16 / FP8 rounding error
+                            shrinks with them.  Rows scored against such a model must be
+                            centred at the same mu: pass rgbd_svm_centre()'s pointer as
+                            x_centre to lbp_fused_features / lbp_normalize_features. */
 
 /* ---- SVM kernels ------------------------------------------------------------------------- */
 #define RGBD_KERNEL_LINEAR 0 /* S_c = w_c . x + b_c */
@@ -90,6 +99,7 @@ typedef struct rgbd_svm_info {
     int32_t scorable;  /* 0 when packed without coefficients */
     float gamma;
     float sv_scale;    /* FP8 per-tensor scale of the SVs (1 otherwise) */
+    int32_t centred;   /* 1 when packed with RGBD_DT_CENTRED */
 } rgbd_svm_info;
 
 /* ======================================================================================= */
@@ -125,6 +135,10 @@ int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear);
  * path; scores change within rounding (the split of the SV sum).
  *   RGBD_TUNE_LBP_CTAS_PER_SM   resident fused-kernel CTAs per SM (1 or 2)
  *   RGBD_TUNE_TC_SPLITS         SV-tile ranges per 128-row block in tensor-core scoring
+ *   RGBD_TUNE_LBP_SHAPE         fused-kernel tile shape: 0 = default (2), 1 = one thread
+ *                               per 8 x 8 cell (crops 64 and 128; CTAs of (crop/8)^2
+ *                               threads), 2 = one thread per 4 x 8 half cell (CTAs of
+ *                               2 (crop/8)^2 threads)
  *   RGBD_TUNE_TC_PAIRING        CTA pairing of 128-row blocks in tensor-core scoring:
  *                               0 = default (3), 2 = no pairing, 3 = each pair runs one
  *                               256-row MMA (tcgen05 cta_group::2, each CTA holding half of
@@ -133,6 +147,7 @@ int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear);
 #define RGBD_TUNE_LBP_CTAS_PER_SM 1
 #define RGBD_TUNE_TC_SPLITS 2
 #define RGBD_TUNE_TC_PAIRING 3
+#define RGBD_TUNE_LBP_SHAPE 4
 int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value);
 
 /* ======================================================================================= */
@@ -219,6 +234,9 @@ int rgbd_crop_affine(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, 
  *          to nearest even) or RGBD_DT_FP8 (E4M3 of x * x_scale, round to
  *          nearest even, saturating); row stride k_pad >= dim, a multiple of
  *          128; columns dim..k_pad-1 are written as 0.  x_dtype 0 = none.
+ *   x_centre  NULL, or device float [dim] (e.g. rgbd_svm_centre() of an
+ *          RGBD_DT_CENTRED model): the rows hold x_j - x_centre[j] (fp32
+ *          difference, round to nearest even) before the conversion above.
  *   xsq_out  NULL or float [n]: sum of squares of the values x_out represents
  *          (for FP8, of the decoded code / x_scale).
  * Errors: RGBD_ERR_ARG, RGBD_ERR_UNSUPPORTED (cell != 8, crop outside the
@@ -226,7 +244,8 @@ int rgbd_crop_affine(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, 
 int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, int n_frames,
                        int H, int W, const rgbd_rect* rects, const int32_t* affine_q16, int n,
                        int crop, int cell, int mask_mm, int flags, uint16_t* feats, int x_dtype,
-                       void* x_out, int k_pad, float x_scale, float* xsq_out, void* stream);
+                       void* x_out, int k_pad, float x_scale, const float* x_centre, float* xsq_out,
+                       void* stream);
 
 /* With flags & RGBD_LBP_FACE_HIST256 the same call computes the paper's own face descriptor
  * (Section 3: one histogram of the raw 8-bit LBP codes, bins 0..255, per face): crop any size
@@ -237,8 +256,8 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
  * stored database, synthetic counts).  feats uint16 [n][dim], dim a multiple
  * of nbins; other arguments as in lbp_fused_features. */
 int lbp_normalize_features(rgbd_ctx* ctx, const uint16_t* feats, int n, int dim, int nbins,
-                           int x_dtype, void* x_out, int k_pad, float x_scale, float* xsq_out,
-                           void* stream);
+                           int x_dtype, void* x_out, int k_pad, float x_scale, const float* x_centre,
+                           float* xsq_out, void* stream);
 
 /* ======================================================================================= */
 /* A5-A7: the SVM (Section 2.5: one-vs-rest, "faces" vs "non-faces" per person)           */
@@ -252,7 +271,12 @@ int lbp_normalize_features(rgbd_ctx* ctx, const uint16_t* feats, int n, int dim,
  *   bias   float [n_classes] (NULL = zeros).
  *   dtype  RGBD_DT_*: how SVs are stored and scored (FP8: per-tensor scale
  *          448 / max|sv|, reported in rgbd_svm_info.sv_scale).  A linear
- *          model is always RGBD_DT_F32.
+ *          model is always RGBD_DT_F32.  An RBF model may add
+ *          RGBD_DT_CENTRED: mu_j = fp32(sum_i x_ij / n_sv), the sum over the
+ *          fp32 normalised SV rows taken in fp64 in row order; the stored rows
+ *          are fp32(x_ij - mu_j) (then the dtype conversion; FP8 scale 448 /
+ *          max|x - mu|), and their squared norms are those of the stored
+ *          values.
  *   coef == NULL packs only the normalised SV matrix (for a host trainer,
  *          Section 3 trains on the CPU); such a model is not scorable.
  * *model_out receives a library-owned handle (free with rgbd_svm_free).
@@ -270,9 +294,16 @@ int rgbd_svm_get_info(const rgbd_svm* model, rgbd_svm_info* info);
  * of the squared norms of its rows (float [n_sv_pad]); either may be NULL. */
 int rgbd_svm_packed_sv(const rgbd_svm* model, const void** sv, const float** sv_sq);
 
+/* *centre receives the device pointer of an RGBD_DT_CENTRED model's mean mu
+ * (float [k_pad], zero past dim; owned by the model), or NULL for a model
+ * packed without centring.  Errors: RGBD_ERR_ARG (NULL arguments). */
+int rgbd_svm_centre(const rgbd_svm* model, const float** centre);
+
 /* Scores n normalised rows.
  *   x       [n][k_pad] in the model's dtype (float for F32 / TF32 / linear),
- *           as written by lbp_fused_features or lbp_normalize_features.
+ *           as written by lbp_fused_features or lbp_normalize_features
+ *           (with the model's centre as x_centre when it was packed with
+ *           RGBD_DT_CENTRED).
  *   xsq     float [n], squared norms of the rows (RBF only; may be NULL for a
  *           linear model).
  *   x_scale FP8 per-tensor scale of x (ignored for other dtypes).

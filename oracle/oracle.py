@@ -20,7 +20,7 @@ import numpy as np
 __all__ = [
     "build", "lib", "rect_coord_q16", "crop", "median_nonzero", "valid_mask", "lbp_code",
     "lbp_codes", "uniform_table", "histograms", "features_batch", "normalize_f64",
-    "normalize_f32", "f32_to_bf16", "f32_to_e4m3", "e4m3_to_f64", "svm_rbf", "svm_linear",
+    "normalize_f32", "sv_centre", "centre_rows", "f32_to_bf16", "f32_to_e4m3", "e4m3_to_f64", "svm_rbf", "svm_linear",
     "argmax", "track_nearest", "track_streams", "face_roi", "CALIB_DTYPE", "svm_train_rbf", "RECT_DTYPE", "LBP_GE", "LBP_NBR_IGNORE_MASK",
 ]
 
@@ -213,6 +213,22 @@ def normalize_f32(feats, nbins=59):
     out = np.zeros((n, dim), np.float32)
     lib().orc_normalize_f32(_p(feats), n, dim // nbins, nbins, _p(out))
     return out
+
+
+def sv_centre(x32):
+    """Column means of normalised fp32 rows (the centre of a model packed with centring): the
+    fp64 sum of each column taken in row order, divided by the row count in fp64, rounded to
+    fp32.  The RBF kernel of Section 2.5 depends only on differences of rows, so subtracting one
+    vector from every row leaves it unchanged."""
+    x = np.asarray(x32, np.float32).astype(np.float64)
+    s = np.cumsum(x, axis=0)[-1]  # a running sum: strictly in row order
+    return (s / np.float64(x.shape[0])).astype(np.float32)
+
+
+def centre_rows(x32, mu):
+    """x - mu per column in fp32 (one IEEE rounding)."""
+    x = np.asarray(x32, np.float32)
+    return (x - np.asarray(mu, np.float32)[: x.shape[1]]).astype(np.float32)
 
 
 def f32_to_bf16(x):

@@ -3,9 +3,10 @@
 It times the two stages of a workload (the fused feature kernel and the scoring kernels) under
 candidate settings of the context's tuning knobs and keeps the fastest:
 
-  K1  resident fused-kernel CTAs per SM (1 or 2): one 512-thread CTA per face works on a
-      128 x 128 crop laid out as 16 x 16 cells of 8 x 8 pixels, two half-cell column tiles per
-      cell, so this picks between one or two such crop tiles in flight per SM;
+  K1  the fused kernel's tile shape and resident CTAs per SM: one CTA per face works on a
+      128 x 128 crop laid out as 16 x 16 cells of 8 x 8 pixels, with either one thread per
+      4 x 8 half cell (512 threads, 64 registers) or one thread per cell (256 threads, up to
+      128 registers), and one or two such CTAs in flight per SM;
   K2  how many SV-tile ranges ("splits") each 128-row block of the tensor-core scoring
       kernel is cut into (the row x SV tiling across SMs), and whether CTA pairs run one
       256-row MMA (tcgen05 cta_group::2) or every CTA runs its own 128-row MMA.
@@ -24,7 +25,7 @@ import torch
 
 from . import binding as B
 
-CACHE_VERSION = 2  # bumped whenever the set of knobs changes
+CACHE_VERSION = 3  # bumped whenever the set of knobs changes
 CACHE_PATH = os.environ.get("RGBD_TUNE_CACHE",
                             os.path.join(os.path.expanduser("~"), ".cache", "rgbd_lbp_gb300", "tune.json"))
 
@@ -34,14 +35,17 @@ class Tuning:
     lbp_ctas_per_sm: int = 0
     tc_splits: int = 0
     tc_pairing: int = 0
+    lbp_shape: int = 0   # fused-kernel threads per cell (2: half cells, 1: whole cells; 0 = default)
 
     def apply(self, ctx):
         ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, self.lbp_ctas_per_sm)
+        ctx.set_tuning(B.TUNE_LBP_SHAPE, self.lbp_shape)
         ctx.set_tuning(B.TUNE_TC_SPLITS, self.tc_splits)
         ctx.set_tuning(B.TUNE_TC_PAIRING, self.tc_pairing)
 
 
 PAIRING_NAMES = {2: "single", 3: "pair"}
+SHAPE_NAMES = {1: "cell", 2: "halfcell"}
 
 
 def _time(fn, stream, reps=3):
@@ -105,14 +109,17 @@ def tune(ctx, key, stage1, stage2, n_rows, n_sv, stream, use_cache=True, tensor_
             return t, dict(cache[full_key], cached=True)
     report = {"k1": {}, "k2": {}}
     best = Tuning()
-    # K1: CTAs per SM
+    # K1: tile shape x CTAs per SM
     best_ms = None
-    for c in (2, 1):
-        ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, c)
-        ms = _time(stage1, stream)
-        report["k1"][c] = ms
-        if best_ms is None or ms < best_ms:
-            best_ms, best.lbp_ctas_per_sm = ms, c
+    for shape in (2, 1):
+        for c in (2, 1):
+            ctx.set_tuning(B.TUNE_LBP_SHAPE, shape)
+            ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, c)
+            ms = _time(stage1, stream)
+            report["k1"][f"{SHAPE_NAMES[shape]}/{c}"] = ms
+            if best_ms is None or ms < best_ms:
+                best_ms, best.lbp_shape, best.lbp_ctas_per_sm = ms, shape, c
+    ctx.set_tuning(B.TUNE_LBP_SHAPE, best.lbp_shape)
     ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, best.lbp_ctas_per_sm)
     # K2: splits x CTA pairing
     if tensor_core:

@@ -21,9 +21,10 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "rgbd_lbp.h")
 
 RGBD_OK = 0
 DT_F32, DT_BF16, DT_FP8, DT_TF32, DT_BF16X3 = 1, 2, 3, 4, 5
+DT_CENTRED = 0x100  # svm_train_data_pack flag: SVs stored relative to their mean
 KERNEL_LINEAR, KERNEL_RBF = 0, 1
 LBP_GE, LBP_NBR_IGNORE_MASK, LBP_FACE_HIST256 = 1, 2, 4
-TUNE_LBP_CTAS_PER_SM, TUNE_TC_SPLITS, TUNE_TC_PAIRING = 1, 2, 3
+TUNE_LBP_CTAS_PER_SM, TUNE_TC_SPLITS, TUNE_TC_PAIRING, TUNE_LBP_SHAPE = 1, 2, 3, 4
 STATUS_BAD_RECT, STATUS_WAIT_TIMEOUT = 1, 2
 NBINS, CELL = 59, 8
 
@@ -42,7 +43,7 @@ class SvmInfo(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n_sv", ctypes.c_int32),
                 ("n_sv_pad", ctypes.c_int32), ("dim", ctypes.c_int32), ("k_pad", ctypes.c_int32),
                 ("n_classes", ctypes.c_int32), ("scorable", ctypes.c_int32), ("gamma", ctypes.c_float),
-                ("sv_scale", ctypes.c_float)]
+                ("sv_scale", ctypes.c_float), ("centred", ctypes.c_int32)]
 
 
 def declared_functions(header: str = HEADER):
@@ -69,12 +70,13 @@ def lib():
             "rgbd_ctx_reserve": [P, Z],
             "rgbd_ctx_status": [P, P, I],
             "rgbd_crop_affine": [P, P, P, I, I, I, P, P, I, I, I, P, P, P],
-            "lbp_fused_features": [P, P, P, I, I, I, P, P, I, I, I, I, I, P, I, P, I, F, P, P],
-            "lbp_normalize_features": [P, P, I, I, I, I, P, I, F, P, P],
+            "lbp_fused_features": [P, P, P, I, I, I, P, P, I, I, I, I, I, P, I, P, I, F, P, P, P],
+            "lbp_normalize_features": [P, P, I, I, I, I, P, I, F, P, P, P],
             "svm_train_data_pack": [P, P, I, I, I, P, P, I, I, F, I, P, P],
             "rgbd_svm_free": [P],
             "rgbd_svm_get_info": [P, P],
             "rgbd_svm_packed_sv": [P, P, P],
+            "rgbd_svm_centre": [P, P],
             "svm_score": [P, P, P, P, I, F, P, P, P],
             "rgbd_ctx_set_tuning": [P, I, I],
             "rgbd_track_nearest": [P, P, I, P, I, P, P],
@@ -111,6 +113,20 @@ def _p(t):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _centre(c):
+    """x_centre argument: None, a device float tensor, or a model packed with DT_CENTRED."""
+    if c is None:
+        return None
+    if isinstance(c, SvmModel):
+        ptr = c.centre_ptr()
+        if ptr is None:
+            raise ValueError("the model was packed without DT_CENTRED")
+        return ctypes.c_void_p(ptr)
+    if c.dtype != torch.float32:
+        raise ValueError("x_centre must be float32")
+    return _p(c)
 
 
 def _stream(stream):
@@ -198,7 +214,8 @@ def rgbd_crop_affine(ctx, grey, depth, rects, out_h, out_w, affine=None, out_gre
 
 
 def lbp_fused_features(ctx, grey, depth, rects=None, crop=128, cell=CELL, mask_mm=150, flags=0, feats=True,
-                       x_dtype=0, k_pad=None, x_scale=448.0, xsq=True, affine=None, out=None, stream=None):
+                       x_dtype=0, k_pad=None, x_scale=448.0, xsq=True, affine=None, out=None, x_centre=None,
+                       stream=None):
     """Returns (feats uint16-as-int16 [n][dim] or None, x [n][k_pad] or None, xsq [n] or None)."""
     F, H, W = grey.shape
     n = F if rects is None else rects.shape[0]
@@ -219,7 +236,8 @@ def lbp_fused_features(ctx, grey, depth, rects=None, crop=128, cell=CELL, mask_m
         q = torch.empty((n,), dtype=torch.float32, device=grey.device)
     _check(lib().lbp_fused_features(ctx.handle, _p(grey), _p(depth), F, H, W, _p(rects), _p(affine), n, crop, cell,
                                     mask_mm, flags, _p(f) if feats else None, dt, _p(x) if dt else None, k_pad,
-                                    float(x_scale), _p(q) if (dt and xsq) else None, _stream(stream)))
+                                    float(x_scale), _centre(x_centre), _p(q) if (dt and xsq) else None,
+                                    _stream(stream)))
     return (f if feats else None), (x if dt else None), (q if (dt and xsq) else None)
 
 
@@ -315,14 +333,15 @@ def rgbd_debug_expm1(z, stream=None):
     return out
 
 
-def lbp_normalize_features(ctx, feats, x_dtype, k_pad=None, x_scale=448.0, nbins=NBINS, stream=None):
+def lbp_normalize_features(ctx, feats, x_dtype, k_pad=None, x_scale=448.0, nbins=NBINS, x_centre=None,
+                           stream=None):
     n, dim = feats.shape
     dt = _dt(x_dtype)
     k_pad = k_pad_for(dim) if k_pad is None else k_pad
     x = torch.empty(x_shape(dt, n, k_pad), dtype=x_torch_dtype(dt), device=feats.device)
     q = torch.empty((n,), dtype=torch.float32, device=feats.device)
     _check(lib().lbp_normalize_features(ctx.handle, _p(feats), n, dim, nbins, dt, _p(x), k_pad, float(x_scale),
-                                        _p(q), _stream(stream)))
+                                        _centre(x_centre), _p(q), _stream(stream)))
     return x, q
 
 
@@ -343,6 +362,23 @@ class SvmModel:
     def dtype(self):
         return self.info.dtype
 
+    @property
+    def centred(self):
+        return bool(self.info.centred)
+
+    def centre_ptr(self):
+        """Device address of the model's centre (float [k_pad]), or None."""
+        p = ctypes.c_void_p()
+        _check(lib().rgbd_svm_centre(self.handle, ctypes.byref(p)))
+        return p.value
+
+    def centre(self):
+        """A copy of the model's centre, float32 [k_pad] on its device (None if uncentred)."""
+        ptr = self.centre_ptr()
+        if ptr is None:
+            return None
+        return torch.as_tensor(_DeviceArray(ptr, self.info.k_pad), device=f"cuda:{torch.cuda.current_device()}").clone()
+
     def free(self):
         if self.handle:
             lib().rgbd_svm_free(self.handle)
@@ -355,8 +391,17 @@ class SvmModel:
             pass
 
 
+class _DeviceArray:
+    """A library-owned float32 device buffer [n], seen by torch through the CUDA array
+    interface (torch.as_tensor makes a view of it without copying)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
 def svm_train_data_pack(ctx, sv_feats, coef, bias=None, kernel=KERNEL_RBF, gamma=None, dtype=DT_F32, dim=None,
-                        nbins=NBINS, stream=None):
+                        nbins=NBINS, centred=False, stream=None):
     if kernel == KERNEL_RBF:
         n_sv, dim = sv_feats.shape
         gamma = 1.0 / dim if gamma is None else gamma
@@ -366,8 +411,9 @@ def svm_train_data_pack(ctx, sv_feats, coef, bias=None, kernel=KERNEL_RBF, gamma
         gamma = 0.0 if gamma is None else gamma
     C = coef.shape[0] if coef is not None else 0
     h = ctypes.c_void_p()
+    dt = _dt(dtype) | (DT_CENTRED if centred else 0)
     _check(lib().svm_train_data_pack(ctx.handle, _p(sv_feats) if sv_feats is not None else None, n_sv, dim, nbins,
-                                     _p(coef), _p(bias), C, kernel, float(gamma), _dt(dtype), ctypes.byref(h),
+                                     _p(coef), _p(bias), C, kernel, float(gamma), dt, ctypes.byref(h),
                                      _stream(stream)))
     return SvmModel(h)
 

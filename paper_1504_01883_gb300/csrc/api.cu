@@ -147,6 +147,10 @@ int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value) {
         case RGBD_TUNE_TC_SPLITS:
             ctx->tune_tc_splits = value;
             return RGBD_OK;
+        case RGBD_TUNE_LBP_SHAPE:
+            CHECK_ARG(value <= 2, "rgbd_ctx_set_tuning: fused-kernel shape %d (0, 1 or 2)", value);
+            ctx->tune_lbp_shape = value;
+            return RGBD_OK;
         case RGBD_TUNE_TC_PAIRING:
             CHECK_ARG(value == 0 || value == 2 || value == 3, "rgbd_ctx_set_tuning: CTA pairing %d (0, 2 or 3)", value);
             ctx->tune_tc_pairing = value;
@@ -191,7 +195,8 @@ static int check_x_out(const char* fn, int dim, int x_dtype, const void* x_out, 
 int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth, int n_frames,
                        int H, int W, const rgbd_rect* rects, const int32_t* affine_q16, int n,
                        int crop, int cell, int mask_mm, int flags, uint16_t* feats, int x_dtype,
-                       void* x_out, int k_pad, float x_scale, float* xsq_out, void* stream) {
+                       void* x_out, int k_pad, float x_scale, const float* x_centre, float* xsq_out,
+                       void* stream) {
     rgbd::NvtxRange nvtx_range("lbp_fused_features");
     CHECK_ARG(ctx != nullptr, "lbp_fused_features: ctx is NULL");
     CHECK_ARG(n >= 0, "lbp_fused_features: n %d < 0", n);
@@ -217,6 +222,7 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
     const int dim = face256 ? 256 : (crop / kCell) * (crop / kCell) * kBins;
     int rc = check_x_out("lbp_fused_features", dim, x_dtype, x_out, k_pad, x_scale);
     if (rc) return rc;
+    CHECK_ARG((reinterpret_cast<uintptr_t>(x_centre) & 15) == 0, "lbp_fused_features: x_centre not 16-byte aligned");
     if (rects == nullptr) {
         CHECK_ARG(affine_q16 == nullptr, "lbp_fused_features: affine needs rects");
         CHECK_ARG(n_frames == n && H == crop && W == crop,
@@ -243,6 +249,7 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
     a.x_out = x_out;
     a.k_pad = k_pad;
     a.x_scale = x_scale;
+    a.x_centre = x_dtype ? x_centre : nullptr;
     a.x_plane = (size_t)n * k_pad;
     a.xsq = xsq_out;
     a.status = ctx->d_status;
@@ -251,8 +258,8 @@ int lbp_fused_features(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
 }
 
 int lbp_normalize_features(rgbd_ctx* ctx, const uint16_t* feats, int n, int dim, int nbins,
-                           int x_dtype, void* x_out, int k_pad, float x_scale, float* xsq_out,
-                           void* stream) {
+                           int x_dtype, void* x_out, int k_pad, float x_scale, const float* x_centre,
+                           float* xsq_out, void* stream) {
     rgbd::NvtxRange nvtx_range("lbp_normalize_features");
     CHECK_ARG(ctx != nullptr, "lbp_normalize_features: ctx is NULL");
     CHECK_ARG(n >= 0 && dim > 0 && nbins > 0 && dim % nbins == 0,
@@ -265,7 +272,7 @@ int lbp_normalize_features(rgbd_ctx* ctx, const uint16_t* feats, int n, int dim,
     CHECK_ARG(feats != nullptr, "lbp_normalize_features: feats is NULL");
     DeviceGuard g(ctx->props.device);
     return launch_normalize(feats, n, dim, nbins, x_dtype, x_out, k_pad, x_scale, xsq_out, nullptr,
-                            (cudaStream_t)stream);
+                            (cudaStream_t)stream, 0, x_centre);
 }
 
 int svm_score(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* xsq, int n,

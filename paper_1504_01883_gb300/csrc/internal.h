@@ -43,6 +43,7 @@ struct rgbd_ctx {
     int tune_lbp_ctas_per_sm = 0;  // 0 = occupancy limit
     int tune_tc_splits = 0;        // 0 = cost model
     int tune_tc_pairing = 0;       // CTA pairing: 0 = auto, 2 = none, 3 = 2-CTA MMA pairs
+    int tune_lbp_shape = 0;        // fused-kernel threads per cell: 0 = auto (2), 1 = one, 2 = two
     uint32_t* d_status = nullptr;  // device status word, followed by kFaceCounters face-queue counters
     uint32_t* d_counters = nullptr;
     uint32_t counter_next = 0;     // next counter of the pool (a launch takes one and zeroes it)
@@ -59,6 +60,7 @@ struct rgbd_svm {
     float gamma = 0.f;
     float sv_scale = 1.f;
     bool scorable = false;
+    float* centre = nullptr;  // RGBD_DT_CENTRED: mu [k_pad], else NULL
     void* sv = nullptr;       // [n_pad][k_pad] of dtype (float for F32 / TF32)
     float* sv_sq = nullptr;   // [n_pad]
     float* coef = nullptr;    // RBF: float [C][n_pad]; linear: float [C][k_pad]
@@ -117,6 +119,7 @@ struct LbpArgs {
     void* x_out;
     int k_pad;
     float x_scale;
+    const float* x_centre;  // NULL, or float [dim] subtracted from the normalised values
     size_t x_plane;  // RGBD_DT_BF16X3: elements from the hi plane to the lo plane
     float* xsq;
     uint32_t* status;
@@ -127,10 +130,16 @@ int launch_lbp_fused(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s);
 // plane: RGBD_DT_BF16X3 offset (elements) of the lo plane; 0 means n * k_pad.
 int launch_normalize(const uint16_t* feats, int n, int dim, int nbins, int x_dtype, void* x_out,
                      int k_pad, float x_scale, float* xsq, float* row_max, cudaStream_t s,
-                     size_t plane = 0);
+                     size_t plane = 0, const float* centre = nullptr);
 
+// fp32 rows [n][k_pad] -> dtype rows (FP8 with `scale`), with the squared norms of the stored
+// values; plane: RGBD_DT_BF16X3 offset of the lo plane (0 means n * k_pad).
 int launch_quantize_f32(const float* src, int n, int k_pad, int x_dtype, void* dst, float scale,
-                        float* sq, cudaStream_t s);
+                        float* sq, cudaStream_t s, size_t plane = 0);
+
+// Column means of fp32 rows [n][k_pad] (fp64 sums in row order, rounded to fp32) into mu[k_pad]
+// (zero past dim), then rows -= mu (fp32), and the largest |value| into *absmax (>= 0).
+int launch_centre_rows(float* rows, int n, int dim, int k_pad, float* mu, float* absmax, cudaStream_t s);
 
 // scoring
 int score_linear(rgbd_ctx* ctx, const rgbd_svm* m, const float* x, int n, float* scores,

@@ -108,23 +108,36 @@ __device__ __forceinline__ uint32_t cmp_msb(uint32_t a, uint32_t b, uint32_t cb)
     return ((a & ~b) | (~(a ^ b) & d)) & 0x80808080u;
 }
 
-template <int S>
+// Slot of quotient-table entry i = 128 n + h: bits 1..5 of h are XOR-ed with the low bits of n.
+// A warp's lanes read values of several cells at once; without the XOR the table's rows are
+// 64 words apart, so equal counts h of different cells fall into the same bank.  The XOR stays
+// inside the row of n.
+__device__ __forceinline__ int qbf_slot(int i) { return i ^ (((i >> 7) & 31) << 1); }
+// The same for two 16-bit indices (count | centres << 7) packed in one word.
+__device__ __forceinline__ uint32_t qbf_slot2(uint32_t w) { return w ^ ((w >> 6) & 0x003E003Eu); }
+
+// Tile shape of the fused kernel: TPC threads per 8 x 8 cell (2: one per 4 x 8 half cell, 1: one
+// per cell), so a CTA of NT = TPC (S/8)^2 threads works on one face; each thread resamples IPT
+// groups of 4 crop pixels.
+template <int S, int TPC = 2>
 struct Cfg {
     static constexpr int G = S / 8;          // cells per side
-    static constexpr int NT = 2 * G * G;     // threads: one per half cell
+    static constexpr int NT = TPC * G * G;   // threads
     static constexpr int SW = S / 4;         // packed words per crop row
+    static constexpr int IPT = S * S / 4 / NT;  // 4-pixel groups per thread
     static constexpr int DIM = G * G * kBins;
     static constexpr int HW = 15;            // histogram words per thread (60 bins / 4)
     static constexpr int MINB = (S == 128) ? 2 : 1;
+    static_assert(TPC == 1 || TPC == 2, "one or two threads per cell");
 };
 
-template <int S>
+template <int S, int TPC = 2>
 struct __align__(16) Smem {
     // grey words with a one-word / one-row clamp-to-edge border ((S + 2) rows of S / 4 + 2
     // words), then mask words; later the uint16 staging row
     uint32_t img[(S + 2) * (S / 4 + 2) + S * S / 4];
     union {
-        uint32_t hist[Cfg<S>::HW * Cfg<S>::NT];  // P5-P6: thread-private 8-bit counts, word (bin/4)*NT + t
+        uint32_t hist[Cfg<S, TPC>::HW * Cfg<S, TPC>::NT];  // P5-P6: thread-private 8-bit counts, word (bin/4)*NT + t
         uint32_t dep[S * S / 2];                 // P1-P4: the crop's depths, two per word, by item
     };
     uint2 colmap[S];                   // taps per crop column, read two at a time (uint4)
@@ -133,11 +146,11 @@ struct __align__(16) Smem {
     uint16_t ncol[S];                  // nearest depth column per crop column (colmap order)
     uint32_t h1[64];                   // coarse depth histogram: key (d - 1) >> 10 (1024 mm bins)
     uint32_t h2[1024];                 // fine histogram ((d - 1) & 1023) inside the median's coarse bin
-    uint32_t cnt[Cfg<S>::NT];          // valid centres per half cell
+    uint32_t cnt[Cfg<S, TPC>::NT];     // valid centres per thread (half cell or cell)
     float nvf[Cfg<S>::G * Cfg<S>::G];  // valid centres per cell (as float) ...
     float rcp[Cfg<S>::G * Cfg<S>::G];  // ... and its IEEE reciprocal (0 for an empty cell)
-    float red[Cfg<S>::NT / 32];
-    uint32_t wsum[Cfg<S>::NT / 32];   // per-warp totals of the fine median histogram
+    float red[Cfg<S, TPC>::NT / 32];
+    uint32_t wsum[Cfg<S, TPC>::NT / 32];  // per-warp totals of the fine median histogram
     uint32_t sink[32];                 // target of the border stores of non-edge lanes
     int info[4];
     rgbd_rect nrect;                   // the next face's rect, copied in during the current face
@@ -147,14 +160,15 @@ struct __align__(16) Smem {
     uint16_t qbf[65 * 128];            // bf16 bits of the quotient h / n, entry 128 n + h (n, h <= 64)
 };
 
-template <int S>
-__global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(LbpArgs a) {
-    using C = Cfg<S>;
+template <int S, int TPC>
+__global__ void __launch_bounds__(Cfg<S, TPC>::NT, Cfg<S, TPC>::MINB) lbp_fused_kernel(LbpArgs a) {
+    using C = Cfg<S, TPC>;
+    constexpr int IPT = C::IPT;
     constexpr int NT = C::NT, SW = C::SW, G = C::G, DIM = C::DIM;
     constexpr int SP = SW + 2;               // words per row of the bordered grey plane
     constexpr int MW_OFF = (S + 2) * SP;     // the mask plane follows it
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<S>& sm = *reinterpret_cast<Smem<S>*>(smem_raw);
+    Smem<S, TPC>& sm = *reinterpret_cast<Smem<S, TPC>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // Uniform-pattern table: code c is uniform when it has at most two 0/1 changes around the
@@ -175,7 +189,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         if (lane == 0) sm.lut[256] = (uint16_t)(((59 >> 2) * NT) * 4 + (59 & 3));
     }
     // Quotient table of the bf16 output: a cell has at most 64 centres, so every normalised value
-    // is one of the 65 x 65 quotients h / n, computed once per CTA exactly as the other output
+    // is one of the 65 x 65 quotients h / n (stored at qbf_slot(128 n + h)), computed once per
+    // CTA exactly as the other output
     // types compute them (IEEE single quotient by the reciprocal and Markstein's one-fma
     // correction, then round to nearest even bf16).  Entry
     // 128 n + h, so that a staged count with its cell's centre count above it is the index.
@@ -184,7 +199,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         const float n_f = (float)n, r_f = n ? __frcp_rn(n_f) : 0.f, h_f = (float)hh;
         const float q0 = __fmul_rn(h_f, r_f);
         const float rem = __fmaf_rn(-q0, n_f, h_f);
-        sm.qbf[i] = __bfloat16_as_ushort(__float2bfloat16_rn(__fmaf_rn(rem, r_f, q0)));
+        sm.qbf[qbf_slot(i)] = __bfloat16_as_ushort(__float2bfloat16_rn(__fmaf_rn(rem, r_f, q0)));
     }
 
     for (int i = tid; i < 65; i += NT) sm.ctab[i] = i < 8 ? 1ull << (8 * i) : 0ull;
@@ -269,7 +284,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             next_face = a.face_counter ? (int)gridDim.x + (int)atomicAdd(a.face_counter, 1u) : face + (int)gridDim.x;
         unsigned long long cnt8 = 0;  // coarse depth histogram, see below
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < IPT; ++k) {
             const int item = tid + k * NT;  // = v * SW + q
             const int v = item / SW, q = item - v * SW;
             uint32_t gw = 0, d01 = 0, d23 = 0;
@@ -287,6 +302,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     const uint16_t* drow = dsrc + (size_t)rm.y * a.W;
                     const uint4* cm4 = reinterpret_cast<const uint4*>(sm.colmap);
                     uint32_t dv[4];
+                    uint32_t accv[4];  // pair windows: (acc + 2^15) per pixel, the rounded value in byte 2
                     if (pair_win) {
 #pragma unroll
                     for (int e2 = 0; e2 < 2; ++e2) {
@@ -303,12 +319,14 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                             // (256 - fy) h0 + fy h1 = 256 h0 + fy (h1 - h0), exactly
                             const uint32_t h0 = __dp4a(__byte_perm(a0, a1, sel), wts, 0u);
                             const uint32_t h1 = __dp4a(__byte_perm(b0, b1, sel), wts, 0u);
-                            const uint32_t acc = h0 * (256u - fy) + h1 * fy;
                             const int e = 2 * e2 + j;
-                            gw |= ((acc + 32768u) >> 16) << (8 * e);
+                            accv[e] = h0 * (256u - fy) + (h1 * fy + 32768u);  // < 2^24
                             dv[e] = __ldg(drow + (j ? (nn >> 16) : (nn & 0xFFFFu)));
                         }
                     }
+                    // byte 2 of each rounded sum is the pixel: gather the four with byte permutes
+                    gw = __byte_perm(__byte_perm(accv[0], accv[1], 0x0062u), __byte_perm(accv[2], accv[3], 0x0062u),
+                                     0x5410u);
                     } else {
 #pragma unroll
                     for (int e2 = 0; e2 < 2; ++e2) {
@@ -360,9 +378,10 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         {
             // coarse histogram of the non-zero depths, keyed by (d - 1) >> 10 (bins of 1024 mm;
             // any monotone key serves the select, and this one needs no test for holes): a thread
-            // holds 32 depths, so eight 8-bit counters in one 64-bit word count keys 0..7 (depths
-            // up to 8192 mm), added from a table; the warp sums them as 16-bit fields (at most 1024
-            // each) and lane 0 adds them to the histogram.  Rarer, larger depths count with atomics.
+            // holds 4 IPT <= 64 depths, so eight 8-bit counters in one 64-bit word count keys 0..7
+            // (depths up to 8192 mm), added from a table; the warp sums them as 16-bit fields (at
+            // most 2048 each) and lane 0 adds them to the histogram.  Rarer, larger depths count
+            // with atomics.
             const unsigned long long ev = cnt8 & 0x00FF00FF00FF00FFull;          // keys 0, 2, 4, 6
             const unsigned long long od = (cnt8 >> 8) & 0x00FF00FF00FF00FFull;   // keys 1, 3, 5, 7
             const uint32_t s02 = __reduce_add_sync(FULL, (uint32_t)ev);
@@ -427,7 +446,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
         int med = -1;
         if (b1 >= 0) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < 2 * IPT; ++i) {
                 const uint32_t dw = sm.dep[2 * (tid + (i >> 1) * NT) + (i & 1)];
                 const uint32_t lo = dw & 0xFFFFu, hi = dw >> 16;
                 if (((lo - 1u) >> 10) == (uint32_t)b1) atomicAdd(&sm.h2[(lo - 1u) & 1023u], 1u);
@@ -480,7 +499,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
             const uint32_t lo = (uint32_t)lo_i;
             const uint32_t width = (med >= 0 && med + mk > lo_i) ? (uint32_t)(med + mk - lo_i) : 0u;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < IPT; ++k) {
                 uint32_t m = 0;
                 const uint2 dd = reinterpret_cast<const uint2*>(sm.dep)[tid + k * NT];
 #pragma unroll
@@ -527,14 +546,20 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
 #pragma unroll
         for (int w = 0; w < C::HW; ++w) sm.hist[w * NT + tid] = 0;  // (the depths are no longer needed)
         {
-            const int c = tid >> 1, h = tid & 1;
+            // the thread's half cell (TPC = 2), or both halves of its cell in turn (TPC = 1)
+            const int c = tid / TPC;
             const int cy = c / G, cx = c - cy * G;
-            const int wc = 2 * cx + h;
             const int r0 = 8 * cy;
-            const bool le = wc == 0, re = wc == SW - 1;
-            const int wl = le ? wc : wc - 1, wr = re ? wc : wc + 1;
             const uint32_t* GW = sm.img;
             const uint32_t* MW = sm.img + MW_OFF;
+            uint32_t nvalid = 0;
+            uint8_t* hb_t = reinterpret_cast<uint8_t*>(sm.hist) + 4 * tid;  // this thread's counters
+#pragma unroll 1
+            for (int hh = 0; hh < 2 / TPC; ++hh) {
+            const int h = TPC == 2 ? (tid & 1) : hh;
+            const int wc = 2 * cx + h;
+            const bool le = wc == 0, re = wc == SW - 1;
+            const int wl = le ? wc : wc - 1, wr = re ? wc : wc + 1;
             // Words holding pixels (x-1 .. x+2), (x .. x+3), (x+1 .. x+4) of a row; past the crop
             // edge a neighbour repeats the edge pixel (the grey plane's border holds the repeats).
             auto row3g = [&](int row, uint32_t& L, uint32_t& M, uint32_t& R) {
@@ -555,8 +580,6 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 R = __byte_perm(c0, r1, 0x4321);
             };
             uint32_t gUL, gUC, gUR, gCL, gCC, gCR, gDL, gDC, gDR;
-            uint32_t nvalid = 0;
-            uint8_t* hb_t = reinterpret_cast<uint8_t*>(sm.hist) + 4 * tid;  // this thread's counters
             if (masked_grey) {
                 // invalid pixels read as grey 0 (P4): no neighbour masks, only the centre's
                 row3g(r0 - 1, gUL, gUC, gUR);
@@ -579,7 +602,6 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     for (int e = 0; e < 4; ++e) hb_t[sm.lut[(code >> (8 * e)) & 0xFFu]] += 1;
                     gUL = gCL; gUC = gCC; gUR = gCR; gCL = gDL; gCC = gDC; gCR = gDR;
                 }
-                sm.cnt[tid] = nvalid;
             } else {
             uint32_t mUL, mUC, mUR, mCL, mCC, mCR, mDL, mDC, mDR;
             row3g(r0 - 1, gUL, gUC, gUR);
@@ -611,24 +633,26 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 gUL = gCL; gUC = gCC; gUR = gCR; gCL = gDL; gCC = gDC; gCR = gDR;
                 mUL = mCL; mUC = mCC; mUR = mCR; mCL = mDL; mCC = mDC; mCR = mDR;
             }
-            sm.cnt[tid] = nvalid;
             }
+            }
+            sm.cnt[tid] = nvalid;
         }
         if (tid == 0 && a.rects) asm volatile("cp.async.wait_all;" ::: "memory");  // the next rect has landed
         __syncthreads();
 
-        // ---- P6: sum the two half-cell histograms into a uint16 staging row ----------------
+        // ---- P6: each cell's histogram (the sum of its two halves) into a uint16 staging row
         uint16_t* stg = reinterpret_cast<uint16_t*>(sm.img);
         {
-            const int c = tid >> 1, h = tid & 1;
-            const uint32_t nv = sm.cnt[2 * c] + sm.cnt[2 * c + 1];
+            // TPC = 2: the two threads of a cell split its words; TPC = 1: one thread per cell
+            const int c = tid / TPC, h = TPC == 2 ? (tid & 1) : 0;
+            const uint32_t nv = TPC == 2 ? sm.cnt[2 * c] + sm.cnt[2 * c + 1] : sm.cnt[c];
             if (h == 0) {
                 sm.nvf[c] = (float)nv;
                 sm.rcp[c] = nv ? __frcp_rn((float)nv) : 0.f;
             }
-            const int w0 = h ? 8 : 0, w1 = h ? C::HW : 8;
+            const int w0 = h ? 8 : 0, w1 = (h || TPC == 1) ? C::HW : 8;
             for (int w = w0; w < w1; ++w) {
-                uint32_t s = sm.hist[w * NT + 2 * c] + sm.hist[w * NT + 2 * c + 1];
+                uint32_t s = TPC == 2 ? sm.hist[w * NT + 2 * c] + sm.hist[w * NT + 2 * c + 1] : sm.hist[w * NT + c];
                 if (masked_grey && w == 0) s -= 64u - nv;  // the invalid centres counted as code 0
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -649,7 +673,8 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                 prefetch_rect_rows(a.grey, a.depth, a.H, a.W, rn, tid, NT);
         }
         float sq = 0.f;
-        const bool wide = x_dtype == RGBD_DT_BF16 && (a.k_pad & 7) == 0 && (DIM & 7) == 0 &&
+        const bool centred = a.x_centre != nullptr;
+        const bool wide = x_dtype == RGBD_DT_BF16 && !centred && (a.k_pad & 7) == 0 && (DIM & 7) == 0 &&
                           ((reinterpret_cast<size_t>(a.feats) | reinterpret_cast<size_t>(a.x_out)) & 15) == 0;
         if (wide) {
             // bf16 rows, 8 values per thread step (16-byte loads and stores)
@@ -662,7 +687,7 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     if (a.feats)
                         *reinterpret_cast<uint4*>(a.feats + (size_t)face * DIM + j) =
                             make_uint4(hv.x & 0x007F007Fu, hv.y & 0x007F007Fu, hv.z & 0x007F007Fu, hv.w & 0x007F007Fu);
-                    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+                    const uint32_t hw[4] = {qbf_slot2(hv.x), qbf_slot2(hv.y), qbf_slot2(hv.z), qbf_slot2(hv.w)};
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         const uint32_t qb = sm.qbf[(hw[e >> 1] >> (16 * (e & 1))) & 0xFFFFu];
@@ -685,13 +710,13 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                     *reinterpret_cast<uint2*>(a.feats + (size_t)face * DIM + j) =
                         make_uint2(hv.x & 0x007F007Fu, hv.y & 0x007F007Fu);
             }
-            if (x_dtype == RGBD_DT_BF16) {
+            if (x_dtype == RGBD_DT_BF16 && !centred) {
                 // bf16 rows: one table read per value
                 uint32_t pk[2] = {0u, 0u};
                 if (j < DIM) {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const uint32_t qb = sm.qbf[((e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0xFFFFu];
+                        const uint32_t qb = sm.qbf[(qbf_slot2(e < 2 ? hv.x : hv.y) >> (16 * (e & 1))) & 0xFFFFu];
                         const float f = __uint_as_float(qb << 16);
                         sq = fmaf(f, f, sq);
                         pk[e >> 1] |= qb << (16 * (e & 1));
@@ -718,8 +743,26 @@ __global__ void __launch_bounds__(Cfg<S>::NT, Cfg<S>::MINB) lbp_fused_kernel(Lbp
                         const float rem = __fmaf_rn(-q0, n_f, h_f);
                         x[e] = __fmaf_rn(rem, r_f, q0);
                     }
+                    if (centred) {  // x - mu, one fp32 rounding
+                        const float4 mu = *reinterpret_cast<const float4*>(a.x_centre + j);
+                        x[0] = __fsub_rn(x[0], mu.x);
+                        x[1] = __fsub_rn(x[1], mu.y);
+                        x[2] = __fsub_rn(x[2], mu.z);
+                        x[3] = __fsub_rn(x[3], mu.w);
+                    }
                 }
-                if (x_dtype == RGBD_DT_BF16X3) {
+                if (x_dtype == RGBD_DT_BF16) {  // centred bf16 rows (round to nearest even)
+                    uint32_t pk[2] = {0u, 0u};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __nv_bfloat16 q = __float2bfloat16_rn(x[e]);
+                        const float f = __bfloat162float(q);
+                        sq = fmaf(f, f, sq);
+                        pk[e >> 1] |= (uint32_t)__bfloat16_as_ushort(q) << (16 * (e & 1));
+                    }
+                    *reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(a.x_out) + (size_t)face * a.k_pad + j) =
+                        make_uint2(pk[0], pk[1]);
+                } else if (x_dtype == RGBD_DT_BF16X3) {
                     // hi = bf16(x) into the first plane, lo = bf16(x - hi) into the second
                     uint32_t ph[2], pl[2];
 #pragma unroll
@@ -969,7 +1012,8 @@ __global__ void __launch_bounds__(F256_THREADS, 1) lbp_face256_kernel(LbpArgs a)
             const uint32_t h = j < 256 ? hist[j] : 0u;
             if (j < 256 && a.feats) a.feats[(size_t)face * 256 + j] = (uint16_t)h;
             if (x_dtype) {
-                const float x = (j < 256 && nvalid) ? (float)h / (float)nvalid : 0.f;
+                float x = (j < 256 && nvalid) ? (float)h / (float)nvalid : 0.f;
+                if (a.x_centre && j < 256) x = __fsub_rn(x, a.x_centre[j]);
                 const size_t idx = (size_t)face * a.k_pad + j;
                 float qv = x;
                 if (x_dtype == RGBD_DT_BF16) {
@@ -1075,7 +1119,7 @@ __device__ __forceinline__ float store_x(void* out, int dtype, size_t idx, float
 
 __global__ void normalize_kernel(const uint16_t* __restrict__ feats, int n, int dim, int nbins,
                                  int x_dtype, void* x_out, int k_pad, float x_scale, float* xsq,
-                                 float* row_max, size_t plane) {
+                                 float* row_max, size_t plane, const float* __restrict__ centre) {
     extern __shared__ uint32_t nv[];  // [dim / nbins]
     __shared__ float red[2][32];
     const int cells = dim / nbins;
@@ -1094,8 +1138,9 @@ __global__ void normalize_kernel(const uint16_t* __restrict__ feats, int n, int 
             if (j < dim) {
                 const uint32_t t = nv[j / nbins];
                 x = t ? (float)h[j] / (float)t : 0.f;
+                if (centre) x = __fsub_rn(x, centre[j]);
             }
-            mx = fmaxf(mx, x);
+            mx = fmaxf(mx, fabsf(x));
             const float q = store_x(x_out, x_dtype, (size_t)row * k_pad + j, x, x_scale, plane);
             sq = fmaf(q, q, sq);
         }
@@ -1123,13 +1168,13 @@ __global__ void normalize_kernel(const uint16_t* __restrict__ feats, int n, int 
 
 // fp32 rows -> dtype rows (FP8 with `scale`), with squared norms of the stored values.
 __global__ void quantize_kernel(const float* __restrict__ src, int n, int k_pad, int dtype, void* dst,
-                                float scale, float* sq_out) {
+                                float scale, float* sq_out, size_t plane) {
     __shared__ float red[32];
     for (int row = blockIdx.x; row < n; row += gridDim.x) {
         __syncthreads();
         float sq = 0.f;
         for (int j = threadIdx.x; j < k_pad; j += blockDim.x) {
-            const float q = store_x(dst, dtype, (size_t)row * k_pad + j, src[(size_t)row * k_pad + j], scale);
+            const float q = store_x(dst, dtype, (size_t)row * k_pad + j, src[(size_t)row * k_pad + j], scale, plane);
             sq = fmaf(q, q, sq);
         }
         for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(FULL, sq, off);
@@ -1143,16 +1188,51 @@ __global__ void quantize_kernel(const float* __restrict__ src, int n, int k_pad,
     }
 }
 
-template <int S>
+// mu[j] = fp32(sum_i rows[i][j] / n), the sum in fp64 in row order (one thread per column, so
+// the order and the result are fixed); mu[j] = 0 for j >= dim.
+__global__ void column_mean_kernel(const float* __restrict__ rows, int n, int dim, int k_pad, float* __restrict__ mu) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k_pad) return;
+    double acc = 0.0;
+    if (j < dim)
+        for (int i = 0; i < n; ++i) acc += (double)rows[(size_t)i * k_pad + j];
+    mu[j] = j < dim ? (float)(acc / (double)n) : 0.f;
+}
+
+// rows[i][j] -= mu[j] (fp32, round to nearest even); *absmax = max |result| (non-negative floats
+// order like their bit patterns, so an integer max serves).
+__global__ void centre_kernel(float* __restrict__ rows, int n, int k_pad, const float* __restrict__ mu,
+                              float* absmax) {
+    __shared__ float red[32];
+    for (int row = blockIdx.x; row < n; row += gridDim.x) {
+        float m = 0.f;
+        for (int j = threadIdx.x; j < k_pad; j += blockDim.x) {
+            const size_t idx = (size_t)row * k_pad + j;
+            const float v = __fsub_rn(rows[idx], mu[j]);
+            rows[idx] = v;
+            m = fmaxf(m, fabsf(v));
+        }
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, off));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+            atomicMax(reinterpret_cast<int*>(absmax), __float_as_int(m));
+        }
+    }
+}
+
+template <int S, int TPC>
 int launch_fused_t(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
     static int blocks_per_sm = -1;
-    const size_t smem = sizeof(Smem<S>);
+    const size_t smem = sizeof(Smem<S, TPC>);
     if (blocks_per_sm < 0) {
-        cudaError_t e = cudaFuncSetAttribute(lbp_fused_kernel<S>,
+        cudaError_t e = cudaFuncSetAttribute(lbp_fused_kernel<S, TPC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: smem attribute");
         int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lbp_fused_kernel<S>, Cfg<S>::NT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lbp_fused_kernel<S, TPC>, Cfg<S, TPC>::NT, smem);
         if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: occupancy");
         blocks_per_sm = b > 0 ? b : 1;
     }
@@ -1162,7 +1242,7 @@ int launch_fused_t(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
         cudaError_t e = cudaMemsetAsync(a.face_counter, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: face queue reset");
     }
-    lbp_fused_kernel<S><<<grid, Cfg<S>::NT, smem, s>>>(a);
+    lbp_fused_kernel<S, TPC><<<grid, Cfg<S, TPC>::NT, smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: launch");
     return RGBD_OK;
@@ -1182,11 +1262,13 @@ int launch_lbp_fused(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: 0-255 histogram launch");
         return RGBD_OK;
     }
+    // tile shape: one thread per cell (tuning value 1, crops 64 and 128), else per half cell
+    const bool per_cell = ctx->tune_lbp_shape == 1;
     switch (a.crop) {
-        case 32: return launch_fused_t<32>(ctx, a, s);
-        case 64: return launch_fused_t<64>(ctx, a, s);
-        case 96: return launch_fused_t<96>(ctx, a, s);
-        case 128: return launch_fused_t<128>(ctx, a, s);
+        case 32: return launch_fused_t<32, 2>(ctx, a, s);
+        case 64: return per_cell ? launch_fused_t<64, 1>(ctx, a, s) : launch_fused_t<64, 2>(ctx, a, s);
+        case 96: return launch_fused_t<96, 2>(ctx, a, s);
+        case 128: return per_cell ? launch_fused_t<128, 1>(ctx, a, s) : launch_fused_t<128, 2>(ctx, a, s);
         default:
             return set_error(RGBD_ERR_UNSUPPORTED, "lbp_fused_features: crop %d (32, 64, 96 or 128)", a.crop);
     }
@@ -1205,25 +1287,37 @@ int launch_crop_affine(rgbd_ctx* ctx, const uint8_t* grey, const uint16_t* depth
 }
 
 int launch_normalize(const uint16_t* feats, int n, int dim, int nbins, int x_dtype, void* x_out,
-                     int k_pad, float x_scale, float* xsq, float* row_max, cudaStream_t s, size_t plane) {
+                     int k_pad, float x_scale, float* xsq, float* row_max, cudaStream_t s, size_t plane,
+                     const float* centre) {
     const int cells = dim / nbins;
     const size_t smem = sizeof(uint32_t) * (size_t)cells;
     if (smem > 48 * 1024) return set_error(RGBD_ERR_UNSUPPORTED, "normalize: %d cells", cells);
     const int grid = std::min(n, 8192);
     if (plane == 0) plane = (size_t)n * k_pad;
     normalize_kernel<<<grid, 256, smem, s>>>(feats, n, dim, nbins, x_dtype, x_out, k_pad, x_scale,
-                                             xsq, row_max, plane);
+                                             xsq, row_max, plane, centre);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "lbp_normalize_features: launch");
     return RGBD_OK;
 }
 
 int launch_quantize_f32(const float* src, int n, int k_pad, int x_dtype, void* dst, float scale,
-                        float* sq, cudaStream_t s) {
+                        float* sq, cudaStream_t s, size_t plane) {
     const int grid = std::min(n, 8192);
-    quantize_kernel<<<grid, 256, 0, s>>>(src, n, k_pad, x_dtype, dst, scale, sq);
+    if (plane == 0) plane = (size_t)n * k_pad;
+    quantize_kernel<<<grid, 256, 0, s>>>(src, n, k_pad, x_dtype, dst, scale, sq, plane);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "quantize: launch");
+    return RGBD_OK;
+}
+
+int launch_centre_rows(float* rows, int n, int dim, int k_pad, float* mu, float* absmax, cudaStream_t s) {
+    column_mean_kernel<<<(k_pad + 255) / 256, 256, 0, s>>>(rows, n, dim, k_pad, mu);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "centre: mean launch");
+    centre_kernel<<<std::min(n, 8192), 256, 0, s>>>(rows, n, k_pad, mu, absmax);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "centre: launch");
     return RGBD_OK;
 }
 

@@ -98,6 +98,7 @@ void free_model(rgbd_svm* m) {
     cudaFree(m->asum);
     cudaFree(m->asum_tile);
     cudaFree(m->bias);
+    cudaFree(m->centre);
     delete m;
 }
 
@@ -135,6 +136,10 @@ int svm_train_data_pack(rgbd_ctx* ctx, const uint16_t* sv_feats, int n_sv, int d
     *model_out = nullptr;
     if (kernel != RGBD_KERNEL_LINEAR && kernel != RGBD_KERNEL_RBF)
         return set_error(RGBD_ERR_ARG, "svm_train_data_pack: kernel %d", kernel);
+    const bool centred = (dtype & RGBD_DT_CENTRED) != 0;
+    dtype &= ~RGBD_DT_CENTRED;
+    if (centred && kernel != RGBD_KERNEL_RBF)
+        return set_error(RGBD_ERR_ARG, "svm_train_data_pack: RGBD_DT_CENTRED applies to RBF models only");
     if (dim <= 0 || nbins <= 0 || nbins > 256 || dim % nbins)
         return set_error(RGBD_ERR_ARG, "svm_train_data_pack: dim %d nbins %d", dim, nbins);
     if (coef && (n_classes <= 0 || n_classes > 256))
@@ -187,7 +192,41 @@ int svm_train_data_pack(rgbd_ctx* ctx, const uint16_t* sv_feats, int n_sv, int d
         TRY_CUDA(cudaMalloc(&m->sv_sq, sizeof(float) * (size_t)m->n_pad), "pack: sv_sq");
         TRY_CUDA(cudaMemsetAsync(m->sv, 0, esz * (size_t)m->n_pad * m->k_pad, s), "pack: sv clear");
         TRY_CUDA(cudaMemsetAsync(m->sv_sq, 0, sizeof(float) * (size_t)m->n_pad, s), "pack: sv_sq clear");
-        if (dtype == RGBD_DT_FP8) {
+        if (centred) {
+            // fp32 rows, their column means mu (fp64 sums), rows - mu, then the dtype conversion
+            // (FP8: per-tensor scale 448 / max|sv - mu|) with the squared norms of the stored values.
+            float* tmp = nullptr;
+            float* d_max = nullptr;
+            TRY_CUDA(cudaMalloc(&m->centre, sizeof(float) * (size_t)m->k_pad), "pack: centre");
+            TRY_CUDA(cudaMalloc(&tmp, sizeof(float) * (size_t)n_sv * m->k_pad), "pack: centring staging");
+            e = cudaMalloc(&d_max, sizeof(float));
+            if (e != cudaSuccess) {
+                cudaFree(tmp);
+                rc = cuda_error(e, "pack: max");
+                free_model(m);
+                return rc;
+            }
+            cudaMemsetAsync(d_max, 0, sizeof(float), s);
+            rc = launch_normalize(sv_feats, n_sv, dim, nbins, RGBD_DT_F32, tmp, m->k_pad, 1.f, nullptr, nullptr, s);
+            if (!rc) rc = launch_centre_rows(tmp, n_sv, dim, m->k_pad, m->centre, d_max, s);
+            float hmax = 0.f;
+            if (!rc && dtype == RGBD_DT_FP8) {
+                e = cudaMemcpyAsync(&hmax, d_max, sizeof(float), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) rc = cuda_error(e, "pack: max readback");
+                m->sv_scale = hmax > 0.f ? 448.f / hmax : 1.f;
+            }
+            if (!rc)
+                rc = launch_quantize_f32(tmp, n_sv, m->k_pad, dtype, m->sv, m->sv_scale, m->sv_sq, s,
+                                         (size_t)m->n_pad * m->k_pad);
+            cudaStreamSynchronize(s);
+            cudaFree(tmp);
+            cudaFree(d_max);
+            if (rc) {
+                free_model(m);
+                return rc;
+            }
+        } else if (dtype == RGBD_DT_FP8) {
             // fp32 rows first, then the per-tensor scale 448 / max|sv|, then E4M3 codes.
             float* tmp = nullptr;
             float* d_max = nullptr;
@@ -283,6 +322,13 @@ int rgbd_svm_get_info(const rgbd_svm* m, rgbd_svm_info* info) {
     info->scorable = m->scorable ? 1 : 0;
     info->gamma = m->gamma;
     info->sv_scale = m->sv_scale;
+    info->centred = m->centre != nullptr ? 1 : 0;
+    return RGBD_OK;
+}
+
+int rgbd_svm_centre(const rgbd_svm* m, const float** centre) {
+    if (!m || !centre) return set_error(RGBD_ERR_ARG, "rgbd_svm_centre: NULL argument");
+    *centre = m->centre;
     return RGBD_OK;
 }
 

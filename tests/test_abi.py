@@ -45,7 +45,7 @@ def test_errors_are_reported_without_a_gpu(built_lib):
     from paper_1504_01883_gb300 import binding
     L = binding.lib()
     rc = L.lbp_fused_features(None, None, None, 0, 0, 0, None, None, 1, 128, 8, 150, 0, None, 0, None, 0,
-                              ctypes.c_float(1.0), None, None)
+                              ctypes.c_float(1.0), None, None, None)
     assert rc == -1
     assert "ctx" in binding.last_error()
     rc = L.svm_score(None, None, None, None, 0, ctypes.c_float(1.0), None, None, None)

@@ -127,6 +127,33 @@ def test_lbp_option_flags(B, ctx, orc, flags):
     assert (host_u16(f) == want).all()
 
 
+@pytest.mark.parametrize("crop", [64, 128])
+@pytest.mark.parametrize("flags", [0, 1, 2])
+def test_tile_shapes_bit_exact(B, ctx, orc, crop, flags):
+    """Both tile shapes of the fused kernel (one thread per cell, one per half cell), one and two
+    CTAs per SM: features bit-exact with the oracle, and the same normalised rows and norms."""
+    g, d, r = synth.frames_with_rects(70 + crop + flags, 3, 7, 40, 256, H=240, W=320)
+    want = orc.features_batch(g, d, r, crop, flags=flags)
+    rows = {}
+    try:
+        for shape in (1, 2):
+            for ctas in (1, 2):
+                ctx.set_tuning(B.TUNE_LBP_SHAPE, shape)
+                ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, ctas)
+                f, x, q = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=crop, flags=flags,
+                                               x_dtype="bf16")
+                assert (host_u16(f) == want).all(), (shape, ctas)
+                rows[(shape, ctas)] = (x.view(torch.int16).cpu().numpy(), q.cpu().numpy())
+    finally:
+        ctx.set_tuning(B.TUNE_LBP_SHAPE, 0)
+        ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, 0)
+    x0, q0 = rows[(2, 2)]
+    for k, (x, q) in rows.items():
+        assert (x == x0).all(), k
+        assert np.allclose(q, q0, rtol=1e-6), k
+    assert ctx.status() == 0
+
+
 def test_general_affine_q16(B, ctx, orc):
     g, d, r = synth.frames_with_rects(8, 2, 3, 60, 160, H=240, W=320)
     n = r.shape[0]
@@ -238,6 +265,68 @@ def test_rbf_tensor_core_paths(B, ctx, orc, dt, n, n_sv, C):
     bound = {"tf32": 2e-5, "bf16": 5e-5, "fp8": 1e-3, "bf16x3": 1e-8}[dt]
     print(f"{dt} n={n} n_sv={n_sv} C={C}: rel err {err:.3e}")
     assert err <= bound, err
+
+
+def test_centred_model_and_rows_bit_exact(B, ctx, orc):
+    """A model packed with centring: its centre equals the oracle's column means of the fp32 SV
+    rows (fp64 sums in row order) bit for bit, and rows centred at it -- from stored counts and
+    from the fused kernel -- equal the oracle's fp32 differences after each conversion."""
+    rng = synth.rng_for(61)
+    dim = 16 * 16 * 59
+    SV = synth.poisson_counts(rng, 700, dim)
+    a, b = synth.rbf_coefficients(rng, 12, 700)
+    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=1.0 / dim, dtype="bf16",
+                                  centred=True)
+    assert model.centred
+    mu = model.centre().cpu().numpy()
+    want_mu = orc.sv_centre(orc.normalize_f32(SV))
+    assert (mu[:dim].view(np.uint32) == want_mu.view(np.uint32)).all()
+    assert (mu[dim:] == 0).all()
+    g, d, r = synth.frames_with_rects(62, 2, 6, 48, 256)
+    counts = orc.features_batch(g, d, r, 128)
+    xc = orc.centre_rows(orc.normalize_f32(counts), mu[:dim])
+    hi = orc.f32_to_bf16(xc)
+    for dt in ["bf16", "f32", "fp8", "bf16x3"]:
+        fused = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=128, feats=False,
+                                     x_dtype=dt, x_centre=model)[1]
+        stored = B.lbp_normalize_features(ctx, dev_u16(counts), dt, x_centre=model)[0]
+        for xs in (fused, stored):
+            if dt == "bf16":
+                assert (host_u16(xs.view(torch.int16))[:, :dim] == hi).all()
+            elif dt == "f32":
+                assert (xs.cpu().numpy()[:, :dim].view(np.uint32) == xc.view(np.uint32)).all()
+                assert (xs.cpu().numpy()[:, dim:] == 0).all()
+            elif dt == "fp8":
+                assert (xs.cpu().numpy()[:, :dim] == orc.f32_to_e4m3((xc * np.float32(448.0)).astype(np.float32))).all()
+            else:
+                planes = host_u16(xs.view(torch.int16))
+                hi_f = (hi.astype(np.uint32) << 16).view(np.float32)
+                assert (planes[0][:, :dim] == hi).all()
+                assert (planes[1][:, :dim] == orc.f32_to_bf16((xc - hi_f).astype(np.float32))).all()
+
+
+@pytest.mark.parametrize("dt", ["bf16", "fp8", "f32", "bf16x3"])
+def test_centred_scores_against_the_oracle(B, ctx, orc, dt):
+    """Scores of a centred model on centred rows against the fp64 oracle of the uncentred
+    problem (centring leaves the RBF kernel unchanged): within each type's bound, and for bf16
+    and FP8 tighter than the same problem scored without centring."""
+    X, SV, a, b, gamma = _scoring_problem(63, 300, 1500, 32)
+    x64, sv64 = orc.normalize_f64(X), orc.normalize_f64(SV)
+    ref = orc.svm_rbf(x64, sv64, a, b, gamma)
+    scale = rbf_error_scale(x64, sv64, a, b, gamma)
+    errs = {}
+    for centred in (False, True):
+        model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype=dt,
+                                      centred=centred)
+        x, q = B.lbp_normalize_features(ctx, dev_u16(X), dt, x_scale=448.0, x_centre=model if centred else None)
+        s, lab = B.svm_score(ctx, model, x, q, x_scale=448.0)
+        assert ctx.status() == 0
+        errs[centred] = rel_score_error(s.cpu().numpy(), ref, scale)
+    bound = {"f32": 1e-5, "bf16": 5e-5, "fp8": 1e-3, "bf16x3": 1e-8}[dt]
+    print(f"{dt}: rel err raw {errs[False]:.3e}, centred {errs[True]:.3e}")
+    assert errs[True] <= bound, errs
+    if dt in ("bf16", "fp8"):
+        assert errs[True] < errs[False], errs
 
 
 def test_epilogue_expm1_accuracy(B):

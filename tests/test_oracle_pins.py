@@ -598,3 +598,32 @@ def test_svm_train_matches_libsvm_and_kkt(orc):
     # a class with no member: every alpha stays 0 and f = b = -1 (all rows are "rest")
     a2, b2, it2 = orc.svm_train_rbf(X, lab, 4, gamma, cost, eps=eps)
     assert (a2[3] == 0).all() and b2[3] == -1.0 and it2[3] == 0
+
+
+# ---- centring of the SVM rows -----------------------------------------------------------------
+
+def test_sv_centre_hand_example(orc):
+    """Column means of three hand-made rows (a row mean or a wrong count would differ)."""
+    x = np.array([[0.25, 1.0, 0.0], [0.75, 0.0, 0.0], [0.5, 0.5, 0.3]], np.float32)
+    mu = orc.sv_centre(x)
+    assert mu.dtype == np.float32
+    assert mu.tolist() == [0.5, 0.5, np.float32(0.1)]
+    c = orc.centre_rows(x, mu)
+    assert c.tolist()[0] == [-0.25, 0.5, -np.float32(0.1)]
+
+
+def test_centred_columns_sum_to_zero_and_rbf_scores_are_unchanged(orc):
+    """Centred columns sum to zero within fp32 rounding, and the fp64 RBF scores of centred
+    rows equal those of the raw rows (the kernel depends only on x - sv)."""
+    rng = np.random.default_rng(5)
+    sv32 = orc.normalize_f32(rng.poisson(3.0, (40, 6 * 59)).astype(np.uint16))
+    x32 = orc.normalize_f32(rng.poisson(3.0, (7, 6 * 59)).astype(np.uint16))
+    mu = orc.sv_centre(sv32)
+    c = orc.centre_rows(sv32, mu).astype(np.float64)
+    assert np.abs(c.sum(0)).max() <= 40 * 2.0 ** -24
+    a = rng.normal(0.0, 1.0, (3, 40))
+    b = rng.normal(0.0, 1.0, 3)
+    g = 1.0 / (6 * 59)
+    raw = orc.svm_rbf(x32.astype(np.float64), sv32.astype(np.float64), a, b, g)
+    cen = orc.svm_rbf(x32.astype(np.float64) - mu, sv32.astype(np.float64) - mu, a, b, g)
+    assert np.abs(raw - cen).max() < 1e-12
