@@ -174,6 +174,7 @@ def _oracle_rows(job):
 
 
 def run_precision(args):
+    import bench
     n_rows, n_sv, C = 65536, 16384, 128
     oracle_rows = int(os.environ.get("PRECISION_ORACLE_ROWS", "64"))
     pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4))  # before any GPU work
@@ -204,8 +205,10 @@ def run_precision(args):
         x, q = B.lbp_normalize_features(ctx, X, dt_base, x_scale=x_scale, x_centre=model if centred else None)
         s_out, l_out = B.svm_score(ctx, model, x, q, x_scale=x_scale)
         torch.cuda.synchronize()
-        reps = 1 if dt == "f32" else 3
+        reps = 1 if dt == "f32" else 20  # ~0.2-1.3 s under load, long enough for the clock samples
         ts = []
+        clocks = bench.ClockSampler(0)
+        clocks.start()
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -214,11 +217,12 @@ def run_precision(args):
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
         ms = float(np.median(ts))
+        clk = clocks.stop()
         flops = 2.0 * n_rows * n_sv * dim + 2.0 * n_rows * n_sv * C
         ratio = {"bf16": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25, "bf16x3": 1.0 / 3.0}.get(dt_base)
         peak = pk["bf16_tflops"] * ratio if ratio else None
         res[dt] = {"ms": ms, "tflops": flops / ms / 1e9, "frac_of_peak": (flops / ms / 1e9) / peak if peak else None,
-                   "peak_tflops": peak}
+                   "peak_tflops": peak, "clocks": clk}
         labels[dt] = l_out.cpu().numpy()
         sub_scores[dt] = s_out[:oracle_rows].cpu().numpy()
         if dt == "f32":
