@@ -154,6 +154,35 @@ def test_tile_shapes_bit_exact(B, ctx, orc, crop, flags):
     assert ctx.status() == 0
 
 
+@pytest.mark.parametrize("crop", [64, 128])
+def test_tile_shapes_on_edge_cases_precut_crops_and_affine(B, ctx, orc, crop):
+    """One thread per cell on the edge frames (all-hole faces, off-frame and bad rects), on
+    pre-cut crops (no rects) and through the general affine path: bit-exact with the oracle."""
+    ctx.set_tuning(B.TUNE_LBP_SHAPE, 1)
+    try:
+        g, d, r = _edge_frames()
+        want = orc.features_batch(g, d, r, crop)
+        ctx.status(clear=True)
+        f, _, _ = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=crop)
+        assert (host_u16(f) == want).all()
+        assert ctx.status() & B.STATUS_BAD_RECT
+        gc, dc = synth.crops(21, 5, crop)
+        f, _, _ = B.lbp_fused_features(ctx, dev_u8(gc), dev_u16(dc), None, crop=crop)
+        assert (host_u16(f) == orc.features_batch(gc, dc, None, crop)).all()
+        g, d, r = synth.frames_with_rects(23, 2, 3, 60, 160, H=240, W=320)
+        n = r.shape[0]
+        aff = np.zeros((n, 6), np.int32)
+        for k in range(n):
+            sc = r[k]["w"] / float(crop)
+            aff[k] = [int(0.9 * sc * 65536), int(-0.3 * sc * 65536), int(r[k]["x"] * 65536),
+                      int(0.3 * sc * 65536), int(0.9 * sc * 65536), int(r[k]["y"] * 65536)]
+        f, _, _ = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=crop,
+                                       affine=torch.from_numpy(aff).cuda())
+        assert (host_u16(f) == orc.features_batch(g, d, r, crop, affine=aff)).all()
+    finally:
+        ctx.set_tuning(B.TUNE_LBP_SHAPE, 0)
+
+
 def test_general_affine_q16(B, ctx, orc):
     g, d, r = synth.frames_with_rects(8, 2, 3, 60, 160, H=240, W=320)
     n = r.shape[0]
@@ -448,6 +477,24 @@ def test_face_histogram_256(B, ctx, orc, crop):
     want2 = orc.features_batch(gc, dc, None, 200, cell=200, nbins=256)
     f2, _, _ = B.lbp_fused_features(ctx, dev_u8(gc), dev_u16(dc), None, crop=200, flags=B.LBP_FACE_HIST256)
     assert (host_u16(f2) == want2).all()
+
+
+def test_face_histogram_256_centred_rows(B, ctx, orc):
+    """Section 3's 0-255 face histogram with rows centred at a given vector: fp32 differences of
+    the oracle's IEEE quotients, bit for bit; a centre that is not 16-byte aligned is rejected."""
+    g, d, r = synth.frames_with_rects(19, 2, 3, 40, 260, H=240, W=320)
+    want = orc.features_batch(g, d, r, 200, cell=200, nbins=256)
+    rng = np.random.default_rng(3)
+    mu = np.zeros(256 + 4, np.float32)
+    mu[:256] = rng.uniform(0.0, 0.02, 256).astype(np.float32)
+    mu_dev = dev_f32(mu)
+    _, x, _ = B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=200,
+                                   flags=B.LBP_FACE_HIST256, x_dtype="f32", x_centre=mu_dev[:256])
+    xc = orc.centre_rows(orc.normalize_f32(want, nbins=256), mu[:256])
+    assert (x.cpu().numpy()[:, :256].view(np.uint32) == xc.view(np.uint32)).all()
+    with pytest.raises(B.RgbdError, match="aligned"):
+        B.lbp_fused_features(ctx, dev_u8(g), dev_u16(d), B.rects_tensor(r), crop=200, flags=B.LBP_FACE_HIST256,
+                             x_dtype="f32", x_centre=mu_dev[1:257])
 
 
 def test_track_nearest(B, ctx, orc):
