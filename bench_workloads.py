@@ -311,13 +311,18 @@ def serving_leg(ctx, seconds, warm_frames=50):
                        "resident",
            "latency": "arrival of the frame -> its scores and labels in host memory",
            "frames": len(events), "offered_crops_per_s": sum(k for _, _, k in events) / seconds}
-    for name, cls in [("batched", serve.BatchServer), ("per_crop", serve.PerCropServer)]:
+    for name, cls in [("batched_native", serve.NativeBatchServer), ("batched", serve.BatchServer),
+                      ("per_crop", serve.PerCropServer)]:
         srv = cls(ctx, model, streams)
         srv.run(events[:warm_frames], realtime=False)  # warm-up
         rep, _ = srv.run(events, realtime=True)
         out[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.summary().items()}
+        if hasattr(srv, "close"):
+            srv.close()
         del srv
         torch.cuda.empty_cache()
+    out["batched_native"]["loop"] = "the library's C++ request loop (rgbd_server)"
+    out["batched"]["loop"] = "Python loop over the C-ABI calls"
     model.free()
     return out
 

@@ -416,6 +416,69 @@ int svm_score_noalloc(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const
                       float x_scale, float* scores, int32_t* labels, void* stream);
 
 /* ======================================================================================= */
+/* Native request loop: continuous batching of camera frames (Sections 2.3-2.5 per frame)  */
+/* ======================================================================================= */
+
+/* A server runs the whole per-frame path -- upload of the frame, fused features of its faces,
+ * scoring against a resident model, per-stream tracking of identities, read-back of the results
+ * -- for frames submitted from any host thread, on a worker thread of its own.  Frames are
+ * admitted into a pool of device frame slots while their bytes fit the pool; frames that
+ * arrive while a batch is on the GPU are uploaded on a copy stream and form the next batch
+ * (all their faces in one fused launch and one scoring launch), so uploads overlap compute and
+ * batches follow each other without a gap.  The server owns its own context (workspace, face
+ * queues); the model must outlive it and is only read. */
+typedef struct rgbd_server_config {
+    int32_t n_slots;          /* device frame slots (frames in flight), 1..1024 */
+    int32_t max_batch_faces;  /* faces per batch, 1..65536; a frame with more is rejected */
+    int32_t H, W;             /* frame size: uint8 grey and uint16 depth planes [H][W] */
+    int32_t crop;             /* 32, 64, 96 or 128 */
+    int32_t mask_mm;          /* depth window around the median, > 0 */
+    int32_t flags;            /* RGBD_LBP_* (not RGBD_LBP_FACE_HIST256) */
+    int32_t n_streams;        /* camera streams tracked, 1..65536 */
+    int32_t max_faces;        /* faces remembered per stream for tracking, 1..256 */
+    float x_scale;            /* FP8 per-tensor scale of the rows (FP8 models), else ignored */
+} rgbd_server_config;
+
+/* One finished request, as returned by rgbd_server_poll. */
+typedef struct rgbd_completion {
+    uint64_t request_id;
+    int32_t status;           /* RGBD_OK, or the error code of the failed call */
+    int32_t n_faces;
+    double t_submit;          /* CLOCK_MONOTONIC seconds at submission ... */
+    double t_done;            /* ... and when the results were in the caller's buffers */
+} rgbd_completion;
+
+typedef struct rgbd_server rgbd_server;
+
+/* Creates a server on the model's device and starts its worker thread.  Allocates the frame
+ * slots (3 H W bytes each), two sets of batch buffers and the tracking state (synchronous).
+ * Errors: RGBD_ERR_ARG (sizes out of range, a model without coefficients), RGBD_ERR_NOMEM. */
+int rgbd_server_create(const rgbd_svm* model, const rgbd_server_config* cfg, rgbd_server** out);
+
+/* Queues one frame of camera stream `stream_id` (0 .. n_streams-1) and returns at once.
+ *   grey uint8 [H][W], depth uint16 [H][W]: host memory (pinned memory lets the upload run
+ *        asynchronously); rects rgbd_rect [n_faces] host memory, the frame field ignored.
+ *   scores float [n_faces][n_classes], labels int32 [n_faces], ids int32 [n_faces] (identities
+ *        after tracking): host memory the results are written to; ids may be NULL.
+ * All buffers are caller-owned and must stay valid, unchanged, until the request completes.
+ * Requests of one stream are served in submission order.  *request_id is its id.
+ * Errors: RGBD_ERR_ARG (NULL pointers, stream id or face count out of range, a stopped server). */
+int rgbd_server_submit(rgbd_server* s, int32_t stream_id, const uint8_t* grey, const uint16_t* depth,
+                       const rgbd_rect* rects, int32_t n_faces, float* scores, int32_t* labels, int32_t* ids,
+                       uint64_t* request_id);
+
+/* Moves up to `max` finished requests into done[] (*n_done of them), waiting up to wait_us
+ * microseconds for the first one when none is ready (0: do not wait). */
+int rgbd_server_poll(rgbd_server* s, rgbd_completion* done, int32_t max, int32_t* n_done, int32_t wait_us);
+
+/* Counters since creation: frames and faces completed, batches launched, admissions that had to
+ * wait for a slot; any pointer may be NULL. */
+int rgbd_server_stats(rgbd_server* s, uint64_t* frames, uint64_t* faces, uint64_t* batches, uint64_t* waits);
+
+/* Serves every queued request, stops the worker and frees the server. */
+int rgbd_server_destroy(rgbd_server* s);
+
+/* ======================================================================================= */
 /* Diagnostics                                                                              */
 /* ======================================================================================= */
 

@@ -85,6 +85,11 @@ def lib():
             "rgbd_face_roi": [P, P, I, I, I, P, P, I, P, P],
             "svm_train_rbf": [P, P, P, I, I, P, I, F, F, F, I, P, P, P, P],
             "rgbd_track_streams": [P, P, P, P, I, I, I, P, P, P, I, P, P, P],
+            "rgbd_server_create": [P, P, P],
+            "rgbd_server_submit": [P, I, P, P, P, I, P, P, P, P],
+            "rgbd_server_poll": [P, P, I, P, I],
+            "rgbd_server_stats": [P, P, P, P, P],
+            "rgbd_server_destroy": [P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -452,3 +457,78 @@ def svm_score_noalloc(ctx, model, x, xsq, x_scale=448.0, scores=None, labels=Non
     _check(fn(ctx.handle, model.handle, _p(x), _p(xsq), n, float(x_scale), _p(scores),
               _p(labels) if want_labels else None, _stream(stream)))
     return scores, (labels if want_labels else None)
+
+
+# ---------------------------------------------------------------------------------------------
+# Native request loop (rgbd_server_*)
+# ---------------------------------------------------------------------------------------------
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("max_batch_faces", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("W", ctypes.c_int32), ("crop", ctypes.c_int32), ("mask_mm", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("n_streams", ctypes.c_int32), ("max_faces", ctypes.c_int32),
+                ("x_scale", ctypes.c_float)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_faces", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class NativeServer:
+    """rgbd_server: the library's own request loop (a worker thread inside the library).
+
+    submit() takes host tensors (pinned for asynchronous uploads) and returns a request id at
+    once; the results land in the host tensors given to submit().  poll() returns finished
+    requests with their submission and completion times (CLOCK_MONOTONIC seconds, the clock of
+    time.clock_gettime(time.CLOCK_MONOTONIC)).  Tensors passed to submit() are kept referenced
+    until their request is polled."""
+
+    def __init__(self, model, H, W, n_streams, n_slots=96, max_batch_faces=2048, crop=128, mask_mm=150, flags=0,
+                 max_faces=16, x_scale=448.0):
+        cfg = ServerConfig(n_slots, max_batch_faces, H, W, crop, mask_mm, flags, n_streams, max_faces, x_scale)
+        h = ctypes.c_void_p()
+        _check(lib().rgbd_server_create(model.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self.model = model  # must outlive the server
+        self.n_classes = model.info.n_classes
+        self._held = {}
+
+    def submit(self, stream_id, grey, depth, rects, scores, labels, ids=None):
+        for t in (grey, depth, rects, scores, labels) + ((ids,) if ids is not None else ()):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("submit takes contiguous host tensors")
+        rid = ctypes.c_uint64()
+        hp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        _check(lib().rgbd_server_submit(self.handle, int(stream_id), hp(grey), hp(depth), hp(rects), int(rects.shape[0]),
+                                        hp(scores), hp(labels), hp(ids), ctypes.byref(rid)))
+        self._held[rid.value] = (grey, depth, rects, scores, labels, ids)
+        return rid.value
+
+    def poll(self, max_n=256, wait_us=0):
+        buf = (Completion * max_n)()
+        n = ctypes.c_int32()
+        _check(lib().rgbd_server_poll(self.handle, buf, max_n, ctypes.byref(n), int(wait_us)))
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            self._held.pop(c.request_id, None)
+            out.append((c.request_id, c.status, c.n_faces, c.t_submit, c.t_done))
+        return out
+
+    def stats(self):
+        v = [ctypes.c_uint64() for _ in range(4)]
+        _check(lib().rgbd_server_stats(self.handle, *[ctypes.byref(x) for x in v]))
+        return {"frames": v[0].value, "faces": v[1].value, "batches": v[2].value, "admission_waits": v[3].value}
+
+    def close(self):
+        if self.handle:
+            lib().rgbd_server_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -382,3 +382,91 @@ class PerCropServer(BatchServer):
             report.batches += k
         report.wall_s = time.perf_counter() - t0
         return report, reqs
+
+
+class NativeBatchServer:
+    """The same continuous batching, run by the library's own request loop (``rgbd_server``: a
+    worker thread in C++ that admits frames into device slots, uploads them on a copy stream and
+    launches batches while the caller only submits frames and collects results).  Python here
+    only replays the arrivals and reads the completion times the library stamps."""
+
+    def __init__(self, ctx, model, streams, n_slots=96, max_faces=2048, crop=128, x_dtype="bf16", mask_mm=150,
+                 device=None):
+        del ctx, x_dtype  # the server has a context of its own and scores in the model's type
+        H, W = streams[0].grey.shape[1:]
+        self.streams = streams
+        self.model = model
+        self.C = model.info.n_classes
+        self.srv = B.NativeServer(model, H, W, n_streams=len(streams), n_slots=n_slots, max_batch_faces=max_faces,
+                                  crop=crop, mask_mm=mask_mm, max_faces=16)
+        self.h_grey = [torch.from_numpy(s.grey).pin_memory() for s in streams]
+        self.h_depth = [torch.from_numpy(s.depth.view(np.int16)).pin_memory() for s in streams]
+        self.h_rects = [[torch.from_numpy(np.ascontiguousarray(r).view(np.int32).reshape(-1, 5)) for r in s.rects]
+                        for s in streams]
+
+    def _submit(self, req):
+        k = req.index % len(self.streams[req.stream].rects)
+        rects = self.h_rects[req.stream][k]
+        n = rects.shape[0]
+        req.n_faces = n
+        req.scores = torch.empty((n, self.C), dtype=torch.float32)
+        req.labels = torch.empty((n,), dtype=torch.int32)
+        req.ids = torch.empty((n,), dtype=torch.int32)
+        return self.srv.submit(req.stream, self.h_grey[req.stream][k], self.h_depth[req.stream][k], rects, req.scores,
+                               req.labels, req.ids)
+
+    def serve_one(self, stream, index):
+        req = FrameRequest(0.0, int(stream), int(index))
+        rid = self._submit(req)
+        while True:
+            done = self.srv.poll(wait_us=100000)
+            if any(d[0] == rid for d in done):
+                break
+        req.scores, req.labels, req.ids = req.scores.numpy(), req.labels.numpy(), req.ids.numpy()
+        return req
+
+    def run(self, events, keep_results=False, realtime=True):
+        counters = collections.Counter()
+        reqs = []
+        for t, s, _ in events:
+            reqs.append(FrameRequest(float(t), int(s), counters[s]))
+            counters[s] += 1
+        if not realtime:
+            for r in reqs:
+                r.t_arrival = 0.0
+        by_id = {}
+        report = ServeReport()
+        b0 = self.srv.stats()["batches"]
+        clock = time.CLOCK_MONOTONIC
+        t0 = time.clock_gettime(clock)
+
+        def collect(wait_us=0):
+            for rid, status, n, _t_sub, t_done in self.srv.poll(wait_us=wait_us):
+                req = by_id.pop(rid)
+                if status != 0:
+                    raise RuntimeError(f"request {rid} failed with status {status}")
+                req.t_done = t_done - t0
+                report.latencies_ms.append(1000.0 * (req.t_done - req.t_arrival))
+                report.frames += 1
+                report.crops += n
+
+        for req in reqs:
+            while True:
+                dt = req.t_arrival - (time.clock_gettime(clock) - t0)
+                if dt <= 0:
+                    break
+                if dt > 0.0005:
+                    time.sleep(dt - 0.0003)
+            by_id[self._submit(req)] = req
+            collect()
+        while by_id:
+            collect(wait_us=1000)
+        report.wall_s = max(r.t_done for r in reqs) if reqs else 0.0
+        report.batches = self.srv.stats()["batches"] - b0
+        if keep_results:
+            for r in reqs:
+                r.scores, r.labels, r.ids = r.scores.numpy(), r.labels.numpy(), r.ids.numpy()
+        return report, reqs
+
+    def close(self):
+        self.srv.close()

@@ -50,6 +50,9 @@ def test_errors_are_reported_without_a_gpu(built_lib):
     assert "ctx" in binding.last_error()
     rc = L.svm_score(None, None, None, None, 0, ctypes.c_float(1.0), None, None, None)
     assert rc == -1
+    out = ctypes.c_void_p()
+    assert L.rgbd_server_create(None, None, ctypes.byref(out)) == -1
+    assert "rgbd_server_create" in binding.last_error()
 
 
 def test_product_path_fails_loudly_without_the_library(monkeypatch, tmp_path):

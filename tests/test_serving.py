@@ -109,3 +109,57 @@ def test_served_identities_follow_the_tracking_rule():
         want = orc.track_streams(state, [req.stream], [0, len(rects)], rects, req.labels)
         assert (req.ids == want).all()
     assert ctx.status() == 0
+
+
+@pytest.mark.gpu
+def test_native_request_loop_matches_the_oracle_and_the_python_loop():
+    """The library's own request loop (rgbd_server): every frame's scores equal its scores served
+    alone and the Python loop's within the bf16 tolerance, labels agree where the top two classes
+    are clear of it, and the identities follow the oracle's Section 2.3 tracking replayed in
+    submission order.  A stream id out of range is rejected at submission."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle as orc
+    from paper_1504_01883_gb300 import _build, serve
+    from paper_1504_01883_gb300 import binding as B
+    _build.build()
+    ctx = B.Context(0)
+    dim = 16 * 16 * 59
+    rng = synth.rng_for(97)
+    sv = synth.poisson_counts(rng, 1024, dim)
+    a, b = synth.rbf_coefficients(rng, 16, 1024)
+    model = B.svm_train_data_pack(ctx, torch.from_numpy(sv.view(np.int16)).cuda(), torch.from_numpy(a).cuda(),
+                                  torch.from_numpy(b).cuda(), gamma=1.0 / dim, dtype="bf16")
+    streams = serve.make_streams(seed=9, n_streams=6, frames_per_stream=3)
+    events = synth.serving_arrivals(seed=9, n_streams=6, seconds=0.3)
+    nat = serve.NativeBatchServer(ctx, model, streams, n_slots=24, max_faces=512)
+    try:
+        rep, reqs = nat.run(events, keep_results=True, realtime=False)  # all at once: mixed batches
+        assert rep.frames == len(events) and rep.batches < len(events)
+        py = serve.BatchServer(ctx, model, streams, n_slots=24, max_faces=512)
+        _, preqs = py.run(events, keep_results=True, realtime=False)
+        scale = np.abs(a).sum(1)[None, :] + np.abs(b)[None, :]
+        for req, pr in zip(reqs, preqs):
+            assert np.max(np.abs(req.scores - pr.scores) / scale) <= 5e-5
+        for req in reqs[:: max(1, len(reqs) // 8)]:
+            one = nat.serve_one(req.stream, req.index)
+            assert np.max(np.abs(one.scores - req.scores) / scale) <= 5e-5
+            srt = np.sort(req.scores, axis=1)
+            clear = (srt[:, -1] - srt[:, -2]) > 5e-5 * scale.max()
+            assert (one.labels[clear] == req.labels[clear]).all()
+        # identities of the mixed run against the oracle's tracking in submission order (the
+        # alone calls above came after it and do not change these results)
+        state = {"rects": np.zeros((6, 16), orc.RECT_DTYPE), "ids": np.full((6, 16), -1, np.int32),
+                 "count": np.zeros(6, np.int32)}
+        for req in reqs:
+            rects = streams[req.stream].rects[req.index % len(streams[req.stream].rects)]
+            want = orc.track_streams(state, [req.stream], [0, len(rects)], rects, req.labels)
+            assert (req.ids == want).all()
+        g = torch.zeros((8, 8), dtype=torch.uint8)
+        with pytest.raises(B.RgbdError, match="stream"):
+            nat.srv.submit(99, g, g.view(torch.int16), torch.zeros((0, 5), dtype=torch.int32),
+                           torch.zeros((0, 16)), torch.zeros((0,), dtype=torch.int32))
+    finally:
+        nat.close()
+    assert ctx.status() == 0
