@@ -314,9 +314,18 @@ def serving_leg(ctx, seconds, warm_frames=50):
     for name, cls in [("batched_native", serve.NativeBatchServer), ("batched", serve.BatchServer),
                       ("per_crop", serve.PerCropServer)]:
         srv = cls(ctx, model, streams)
-        srv.run(events[:warm_frames], realtime=False)  # warm-up
+        # warm-up: large batches (every frame at once), then a short real-time stretch (small
+        # batches), so that no first use of a launch shape or a workspace growth lands in the run
+        srv.run(events[:warm_frames], realtime=False)
+        srv.run(events[:4 * warm_frames], realtime=True)
         rep, _ = srv.run(events, realtime=True)
         out[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in rep.summary().items()}
+        if name != "per_crop":
+            # capacity: every frame of the run queued at once (the per-crop path's real-time run
+            # already falls behind, so its crops/s is its capacity)
+            cap, _ = srv.run(events, realtime=False)
+            out[name]["capacity_crops_per_s"] = round(cap.crops / cap.wall_s, 1)
+            out[name]["capacity_batches"] = cap.batches
         if hasattr(srv, "close"):
             srv.close()
         del srv

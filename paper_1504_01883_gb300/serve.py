@@ -418,10 +418,13 @@ class NativeBatchServer:
     def serve_one(self, stream, index):
         req = FrameRequest(0.0, int(stream), int(index))
         rid = self._submit(req)
+        deadline = time.monotonic() + 60.0
         while True:
             done = self.srv.poll(wait_us=100000)
             if any(d[0] == rid for d in done):
                 break
+            if time.monotonic() > deadline:
+                raise RuntimeError(f"request {rid} did not complete within 60 s")
         req.scores, req.labels, req.ids = req.scores.numpy(), req.labels.numpy(), req.ids.numpy()
         return req
 
@@ -459,8 +462,14 @@ class NativeBatchServer:
                     time.sleep(dt - 0.0003)
             by_id[self._submit(req)] = req
             collect()
+        deadline = time.monotonic() + 60.0
         while by_id:
+            left = len(by_id)
             collect(wait_us=1000)
+            if len(by_id) < left:
+                deadline = time.monotonic() + 60.0
+            elif time.monotonic() > deadline:
+                raise RuntimeError(f"{len(by_id)} requests did not complete within 60 s")
         report.wall_s = max(r.t_done for r in reqs) if reqs else 0.0
         report.batches = self.srv.stats()["batches"] - b0
         if keep_results:
