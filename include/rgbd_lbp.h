@@ -422,7 +422,9 @@ int svm_score_noalloc(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const
 /* A server runs the whole per-frame path -- upload of the frame, fused features of its faces,
  * scoring against a resident model, per-stream tracking of identities, read-back of the results
  * -- for frames submitted from any host thread, on a worker thread of its own.  Frames are
- * admitted into a pool of device frame slots while their bytes fit the pool; frames that
+ * admitted, in submission order, into a pool of device frame slots while a slot is free and
+ * their bytes (the planes, and per face the rows it occupies until done) fit the pool's budget
+ * (the bytes of all slots and of two full batches); frames that
  * arrive while a batch is on the GPU are uploaded on a copy stream and form the next batch
  * (all their faces in one fused launch and one scoring launch), so uploads overlap compute and
  * batches follow each other without a gap.  The server owns its own context (workspace, face

@@ -97,6 +97,8 @@ struct rgbd_server {
     cudaStream_t compute = nullptr, copy = nullptr;
     std::vector<cudaEvent_t> slot_ev;  // upload of each slot done
     std::vector<int> free_slots;
+    size_t frame_bytes = 0, face_bytes = 0;  // device bytes a frame holds while in flight
+    size_t budget = 0, used = 0;              // admission: bytes of the pool frames draw on
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request> incoming;      // submitted, not yet seen by the worker
@@ -189,6 +191,7 @@ void finish(rgbd_server* s, Batch& b) {
             if (r.ids) memcpy(r.ids, bb.h_ids + off, sizeof(int32_t) * (size_t)r.n);
         }
         off += r.n;
+        if (r.slot >= 0) s->used -= s->frame_bytes + (size_t)r.n * s->face_bytes;
         rgbd_completion c;
         c.request_id = r.id;
         c.status = b.status;
@@ -238,10 +241,13 @@ void worker_main(rgbd_server* s) {
             inflight.pop_front();
             progress = true;
         }
-        // admission: every waiting frame that finds a free slot is uploaded, in arrival order
-        while (!waiting.empty() && !s->free_slots.empty()) {
+        // admission, in arrival order: a frame needs a free slot and its bytes (planes, and per
+        // face the rows it occupies until done) within the pool's budget
+        while (!waiting.empty() && !s->free_slots.empty() &&
+               s->used + s->frame_bytes + (size_t)waiting.front().n * s->face_bytes <= s->budget) {
             Request r = waiting.front();
             waiting.pop_front();
+            s->used += s->frame_bytes + (size_t)r.n * s->face_bytes;
             r.slot = s->free_slots.back();
             s->free_slots.pop_back();
             if (r.waited) s->waits++;
@@ -391,6 +397,10 @@ int rgbd_server_create(const rgbd_svm* model, const rgbd_server_config* cfg, rgb
         return rc;
     }
     for (int i = c.n_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->frame_bytes = 3 * plane;
+    s->face_bytes = x_elem_bytes(s->x_dtype) * (size_t)s->k_pad + sizeof(float) * (1 + (size_t)s->C) +
+                    3 * sizeof(int32_t) + sizeof(rgbd_rect);
+    s->budget = ns * s->frame_bytes + 2 * nb * s->face_bytes;
     try {
         s->worker = std::thread(worker_main, s);
     } catch (...) {
