@@ -653,6 +653,34 @@ def test_full_batch_workload_sampled(B, ctx, orc):
     assert (lab.cpu().numpy()[idx][clear] == orc.argmax(ref)[clear]).all()
 
 
+@pytest.mark.parametrize("dt,centred,bound", [("bf16", False, 5e-5), ("bf16", True, 5e-5), ("fp8", False, 1e-3)])
+def test_precision_workload_full_size_sampled(B, ctx, orc, dt, centred, bound):
+    """The precision workload at its full size (65536 rows x 16384 SVs x 15104 dims, 128
+    classes) in the default launch layout: 12 sampled rows' scores within the type's bound of the
+    fp64 oracle, labels equal wherever the fp64 margin clears twice that bound."""
+    dim, n_rows, n_sv, C = 16 * 16 * 59, 65536, 16384, 128
+    X = synth.poisson_counts_device(1507, n_rows, dim, "cuda")
+    SV = synth.poisson_counts_device(1508, n_sv, dim, "cuda")
+    a, b = synth.rbf_coefficients(synth.rng_for(1509), C, n_sv)
+    gamma = 1.0 / dim
+    model = B.svm_train_data_pack(ctx, SV, dev_f32(a), dev_f32(b), gamma=gamma, dtype=dt, centred=centred)
+    x, q = B.lbp_normalize_features(ctx, X, dt, x_scale=448.0, x_centre=model if centred else None)
+    s, lab = B.svm_score(ctx, model, x, q, x_scale=448.0)
+    assert ctx.status() == 0
+    idx = np.linspace(0, n_rows - 1, 12).astype(int)
+    xs = X[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint16)
+    x64, sv64 = orc.normalize_f64(xs), orc.normalize_f64(SV.cpu().numpy().view(np.uint16))
+    ref = orc.svm_rbf(x64, sv64, a, b, gamma)
+    scale = rbf_error_scale(x64, sv64, a, b, gamma)
+    err = rel_score_error(s.cpu().numpy()[idx], ref, scale)
+    print(f"{dt} centred={centred}: rel err {err:.3e}")
+    assert err <= bound, err
+    srt = np.sort(ref, axis=1)
+    clear = (srt[:, -1] - srt[:, -2]) > 2 * bound * scale.max()
+    assert (lab.cpu().numpy()[idx][clear] == orc.argmax(ref)[clear]).all()
+    model.free()
+
+
 def test_empty_inputs(B, ctx, orc):
     """Every batch entry point accepts zero items: nothing is launched, nothing is flagged."""
     g, d, _ = synth.frames_with_rects(3, 1, 1, 48, 64, H=64, W=64)
