@@ -106,6 +106,15 @@ struct TcParams {
     uint32_t idesc_main;
     uint32_t idesc_second;
     int passes;       // 1, or 3 for split bf16 operands (RGBD_DT_BF16X3)
+    // split combine inside the kernel (fuse = 1): the last CTA of each 128-row block to finish
+    // adds the splits of its rows (counters[row block] counts finished splits, zeroed per launch)
+    int fuse;
+    uint32_t* counters;
+    const float* asum;       // [C]
+    const float* asum_tile;  // [n_tiles][C_pad]
+    const float* bias;       // [C]
+    float* scores;           // [n][C]
+    int32_t* labels;         // [n] or NULL
 };
 
 // ---------------------------------------------------------------------------------------
@@ -338,6 +347,81 @@ __device__ __forceinline__ float expm1_near0(float z) {
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+
+// ---------------------------------------------------------------------------------------
+// Split combine (A7), run by the last CTA of a 128-row block to finish: for each row and class
+//   S_c = exp(-gamma r*) (asum_c + sum_s [D_s + delta_s (asum_{c,s} + D_s)]) + b_c,
+// delta_s = expm1(-gamma (r_s - r*)), r* = r_0, asum_{c,s} the coefficient sum of split s's
+// tiles -- the same terms in the same order as reduce_scores_kernel -- then the argmax (lowest
+// class on ties).  The other splits' partial sums are read past L1 (__ldcg): their CTAs fenced
+// them before counting themselves finished.  `work` is shared memory of combine_bytes().
+// ---------------------------------------------------------------------------------------
+__host__ __device__ inline size_t combine_bytes(int splits, int C_pad) {
+    return sizeof(float) * ((size_t)splits * C_pad + (size_t)splits * BM + BM + (size_t)BM * C_pad);
+}
+
+__device__ __noinline__ void combine_splits(const TcParams& p, int m0, int splits, float* work) {
+    const int C = p.C, Cs = p.C_pad, tid = threadIdx.x, nth = blockDim.x;
+    float* s_as = work;                          // [splits][C_pad]
+    float* s_delta = s_as + (size_t)splits * Cs;  // [splits][BM]
+    float* s_esc = s_delta + (size_t)splits * BM;  // [BM]
+    float* s_sc = s_esc + BM;                     // [BM][C_pad]
+    for (int i = tid; i < splits * Cs; i += nth) {
+        const int sp = i / Cs, c = i - sp * Cs;
+        float v = 0.f;
+        if (sp > 0 && c < C)
+            for (int t = sp * p.tiles_per_split; t < min(p.n_tiles, (sp + 1) * p.tiles_per_split); ++t)
+                v += __ldg(p.asum_tile + (size_t)t * Cs + c);
+        s_as[i] = v;
+    }
+    for (int i = tid; i < splits * BM; i += nth) {
+        const int sp = i / BM, rl = i - sp * BM, row = m0 + rl;
+        float d = 0.f;
+        if (row < p.n) {
+            const float rstar = __ldcg(p.ref + row);
+            if (sp > 0) d = expm1f(-p.gamma * (__ldcg(p.ref + (size_t)sp * p.n + row) - rstar));
+            else s_esc[rl] = expf(-p.gamma * rstar);
+        }
+        s_delta[i] = d;
+    }
+    __syncthreads();
+    for (int i = tid; i < BM * C; i += nth) {
+        const int rl = i / C, c = i - rl * C, row = m0 + rl;
+        if (row >= p.n) continue;
+        float acc = 0.f;
+        for (int sp = 0; sp < splits; ++sp) {
+            const float d = __ldcg(p.part + ((size_t)sp * p.n + row) * Cs + c);
+            acc += d + s_delta[sp * BM + rl] * (s_as[sp * Cs + c] + d);
+        }
+        const float sc = s_esc[rl] * (__ldg(p.asum + c) + acc) + __ldg(p.bias + c);
+        p.scores[(size_t)row * C + c] = sc;
+        s_sc[rl * Cs + c] = sc;
+    }
+    if (!p.labels) return;
+    __syncthreads();
+    const int lane = tid & 31;
+    for (int rl = tid >> 5; rl < BM; rl += nth >> 5) {
+        if (m0 + rl >= p.n) continue;
+        float best = -INFINITY;
+        int bi = 0x7FFFFFFF;
+        for (int c = lane; c < C; c += 32) {
+            const float v = s_sc[rl * Cs + c];
+            if (v > best) {
+                best = v;
+                bi = c;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const float ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+            const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, off);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) p.labels[m0 + rl] = bi;
+    }
+}
 
 // ---------------------------------------------------------------------------------------
 // The kernel
@@ -786,6 +870,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 }
             }
             if (row_ok) p.ref[(size_t)split * p.n + grow] = r;
+            if (p.fuse) __threadfence();  // this split's sums are visible before it counts as done
         }
     }
 
@@ -804,6 +889,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         else
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                          : "memory");
+    }
+    if (p.fuse) {
+        // the last split of this row block to finish adds them all; the ring's shared memory is
+        // free now (every copy and MMA of the CTA has completed)
+        __shared__ int last;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last = atomicAdd(p.counters + blockIdx.x, 1u) == gridDim.y - 1;
+        }
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the ring was the async proxy's
+            combine_splits(p, m0, (int)gridDim.y, reinterpret_cast<float*>(gbase));
+        }
     }
 }
 
@@ -897,7 +997,7 @@ struct TcPlan {
     int esz, kind, passes, splits, tps, mt, nt;
     uint32_t fmt;
     CUtensorMapDataType dt;
-    size_t off_ref, bytes;
+    size_t off_ref, off_cnt, bytes;
 };
 
 int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
@@ -931,7 +1031,8 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
     const size_t part_bytes = sizeof(float) * (size_t)pl->splits * n * m->C_pad;
     const size_t ref_bytes = sizeof(float) * (size_t)pl->splits * n;
     pl->off_ref = (part_bytes + 255) & ~size_t(255);
-    pl->bytes = pl->off_ref + ref_bytes;
+    pl->off_cnt = (pl->off_ref + ref_bytes + 255) & ~size_t(255);
+    pl->bytes = pl->off_cnt + sizeof(uint32_t) * (size_t)((pl->mt + 1) / 2 * 2);  // one counter per row block
     return RGBD_OK;
 }
 
@@ -1003,6 +1104,23 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     p.idesc_main = make_idesc(pl.fmt, pl.fmt, mma_m, BN);
     p.idesc_second = make_idesc(1, 1, mma_m, m->C_pad);
     p.passes = pl.passes;
+    // Small batches (up to 8 row blocks) combine their splits inside the kernel, in the last CTA
+    // of each row block to finish, which saves a launch on the latency path of a serving batch;
+    // larger ones leave it to reduce_scores_kernel, which spreads the work over every SM instead
+    // of adding a tail to the last CTAs (on the 4096-row batch the fused combine cost ~9 us more).
+    // The combine also needs its shared memory to fit the ring (every mode's holds >= 140 KB).
+    p.fuse = (pl.mt <= 8 && combine_bytes(pl.splits, m->C_pad) <= (size_t)140 * 1024) ? 1 : 0;
+    p.counters = reinterpret_cast<uint32_t*>(ws + pl.off_cnt);
+    p.asum = m->asum;
+    p.asum_tile = m->asum_tile;
+    p.bias = m->bias;
+    p.scores = scores;
+    p.labels = labels;
+    if (p.fuse) {
+        const cudaError_t ez =
+            cudaMemsetAsync(p.counters, 0, sizeof(uint32_t) * (size_t)((pl.mt + 1) / 2 * 2), s);
+        if (ez != cudaSuccess) return cuda_error(ez, "svm_score: split counters");
+    }
     cudaError_t e;
     switch (mode * 4 + pl.kind) {
         case MODE_SINGLE * 4 + 0: e = launch_mode<MODE_SINGLE, 0>(pl, p, m, tm_x, tm_x2, s); break;
@@ -1015,6 +1133,7 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
         default: e = launch_mode<MODE_PAIR, 3>(pl, p, m, tm_x, tm_x2, s); break;
     }
     if (e != cudaSuccess) return cuda_error(e, "svm_score: tc launch");
+    if (p.fuse) return RGBD_OK;
     return launch_reduce_scores(part, ref, pl.splits, n, m->C, m->C_pad, m->asum, m->asum_tile, pl.tps, pl.nt,
                                 m->bias, m->gamma, scores, labels, s);
 }
