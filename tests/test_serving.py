@@ -163,3 +163,50 @@ def test_native_request_loop_matches_the_oracle_and_the_python_loop():
     finally:
         nat.close()
     assert ctx.status() == 0
+
+
+@pytest.mark.gpu
+def test_native_loop_edge_cases():
+    """Frames without faces pass through, a frame with more faces than a batch holds is
+    rejected, and destroying the server with requests still queued (more than its frame slots)
+    serves them first: every copy of the same frame gets the same scores."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1504_01883_gb300 import _build, serve
+    from paper_1504_01883_gb300 import binding as B
+    _build.build()
+    ctx = B.Context(0)
+    dim = 16 * 16 * 59
+    rng = synth.rng_for(96)
+    sv = synth.poisson_counts(rng, 256, dim)
+    a, b = synth.rbf_coefficients(rng, 8, 256)
+    model = B.svm_train_data_pack(ctx, torch.from_numpy(sv.view(np.int16)).cuda(), torch.from_numpy(a).cuda(),
+                                  torch.from_numpy(b).cuda(), gamma=1.0 / dim, dtype="bf16")
+    streams = serve.make_streams(seed=11, n_streams=2, frames_per_stream=2)
+    H, W = streams[0].grey.shape[1:]
+    srv = B.NativeServer(model, H, W, n_streams=2, n_slots=4, max_batch_faces=16)
+    g = torch.from_numpy(streams[0].grey[0]).pin_memory()
+    d = torch.from_numpy(streams[0].depth[0].view(np.int16)).pin_memory()
+    rects = torch.from_numpy(np.ascontiguousarray(streams[0].rects[0]).view(np.int32).reshape(-1, 5))
+    n = rects.shape[0]
+    none = torch.zeros((0, 5), dtype=torch.int32)
+    ids = []
+    outs = []
+    for k in range(12):  # more than the slots: the queue drains through them
+        r = rects if k % 3 else none
+        sc = torch.empty((r.shape[0], 8))
+        lb = torch.empty((r.shape[0],), dtype=torch.int32)
+        outs.append((r.shape[0], sc, lb))
+        ids.append(srv.submit(k % 2, g, d, r, sc, lb))
+    big = torch.zeros((17, 5), dtype=torch.int32)
+    with pytest.raises(B.RgbdError, match="faces"):
+        srv.submit(0, g, d, big, torch.empty((17, 8)), torch.empty((17,), dtype=torch.int32))
+    srv.close()  # serves the queued requests before it stops
+    ref = None
+    for nf, sc, lb in outs:
+        if nf:
+            ref = sc if ref is None else ref
+            assert torch.allclose(sc, ref, rtol=0, atol=5e-5 * float(np.abs(a).sum(1).max()))
+    assert ref is not None and n > 0
+    assert ctx.status() == 0
