@@ -445,6 +445,8 @@ typedef struct rgbd_server_config {
 typedef struct rgbd_completion {
     uint64_t request_id;
     int32_t status;           /* RGBD_OK, or the error code of the failed call */
+    uint32_t flags;           /* RGBD_STATUS_* raised on the device by the request's batch (e.g. a
+                                 bad rect, whose face gets zero features) */
     int32_t n_faces;
     double t_submit;          /* CLOCK_MONOTONIC seconds at submission ... */
     double t_done;            /* ... and when the results were in the caller's buffers */

@@ -471,8 +471,8 @@ class ServerConfig(ctypes.Structure):
 
 
 class Completion(ctypes.Structure):
-    _fields_ = [("request_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_faces", ctypes.c_int32),
-                ("t_submit", ctypes.c_double), ("t_done", ctypes.c_double)]
+    _fields_ = [("request_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("n_faces", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 class NativeServer:
@@ -513,7 +513,7 @@ class NativeServer:
         for i in range(n.value):
             c = buf[i]
             self._held.pop(c.request_id, None)
-            out.append((c.request_id, c.status, c.n_faces, c.t_submit, c.t_done))
+            out.append((c.request_id, c.status, c.n_faces, c.t_submit, c.t_done, c.flags))
         return out
 
     def stats(self):

@@ -61,6 +61,7 @@ struct BatchBuf {
     float* h_scores = nullptr;
     int32_t* h_labels = nullptr;
     int32_t* h_ids = nullptr;
+    uint32_t* h_status = nullptr;  // the context's status word after the batch
     cudaEvent_t done = nullptr;
     bool busy = false;
 };
@@ -175,6 +176,10 @@ int launch(rgbd_server* s, Batch& b) {
                                 s->compute);
         if (e != cudaSuccess) return rgbd::cuda_error(e, "rgbd_server: result read-back");
     }
+    // the batch's device status flags, read back and cleared for the next batch
+    e = cudaMemcpyAsync(bb.h_status, s->ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->compute);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->ctx->d_status, 0, sizeof(uint32_t), s->compute);
+    if (e != cudaSuccess) return rgbd::cuda_error(e, "rgbd_server: status read-back");
     return RGBD_OK;
 }
 
@@ -195,6 +200,7 @@ void finish(rgbd_server* s, Batch& b) {
         rgbd_completion c;
         c.request_id = r.id;
         c.status = b.status;
+        c.flags = (b.owns_buf && b.status == RGBD_OK) ? *bb.h_status : 0u;
         c.n_faces = r.n;
         c.t_submit = r.t_submit;
         c.t_done = now_s();
@@ -300,6 +306,7 @@ void free_server(rgbd_server* s) {
         cudaFreeHost(bb.h_scores);
         cudaFreeHost(bb.h_labels);
         cudaFreeHost(bb.h_ids);
+        cudaFreeHost(bb.h_status);
         if (bb.done) cudaEventDestroy(bb.done);
     }
     for (cudaEvent_t e : s->slot_ev)
@@ -383,6 +390,7 @@ int rgbd_server_create(const rgbd_svm* model, const rgbd_server_config* cfg, rgb
         pin((void**)&bb.h_scores, sizeof(float) * nb * s->C);
         pin((void**)&bb.h_labels, sizeof(int32_t) * nb);
         pin((void**)&bb.h_ids, sizeof(int32_t) * nb);
+        pin((void**)&bb.h_status, sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bb.done, cudaEventDisableTiming);
     }
     s->slot_ev.assign(ns, nullptr);

@@ -444,7 +444,7 @@ class NativeBatchServer:
         t0 = time.clock_gettime(clock)
 
         def collect(wait_us=0):
-            for rid, status, n, _t_sub, t_done in self.srv.poll(wait_us=wait_us):
+            for rid, status, n, _t_sub, t_done, _flags in self.srv.poll(wait_us=wait_us):
                 req = by_id.pop(rid)
                 if status != 0:
                     raise RuntimeError(f"request {rid} failed with status {status}")

@@ -202,6 +202,24 @@ def test_native_loop_edge_cases():
     big = torch.zeros((17, 5), dtype=torch.int32)
     with pytest.raises(B.RgbdError, match="faces"):
         srv.submit(0, g, d, big, torch.empty((17, 8)), torch.empty((17,), dtype=torch.int32))
+    # a rect of zero width: the face gets zero features and its batch reports the flag
+    bad = rects[:1].clone()
+    bad[0, 3] = 0
+    bad_id = srv.submit(0, g, d, bad, torch.empty((1, 8)), torch.empty((1,), dtype=torch.int32))
+    flags = None
+    for _ in range(200):
+        for c in srv.poll(wait_us=50000):
+            if c[0] == bad_id:
+                flags = c[5]
+        if flags is not None:
+            break
+    assert flags is not None and flags & B.STATUS_BAD_RECT
+    for k in range(12):  # queue more than the slots again, then stop with them pending
+        r = rects if k % 3 else none
+        sc = torch.empty((r.shape[0], 8))
+        lb = torch.empty((r.shape[0],), dtype=torch.int32)
+        outs.append((r.shape[0], sc, lb))
+        srv.submit(k % 2, g, d, r, sc, lb)
     srv.close()  # serves the queued requests before it stops
     ref = None
     for nf, sc, lb in outs:
