@@ -427,8 +427,10 @@ int svm_score_noalloc(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const
  * (the bytes of all slots and of two full batches); frames that
  * arrive while a batch is on the GPU are uploaded on a copy stream and form the next batch
  * (all their faces in one fused launch and one scoring launch), so uploads overlap compute and
- * batches follow each other without a gap.  The server owns its own context (workspace, face
- * queues); the model must outlive it and is only read. */
+ * batches follow each other without a gap.  While work is in flight the worker polls its
+ * events (spinning with yields: one host core for latency); idle, it sleeps until a submission.
+ * The server owns its own context (workspace, face queues); the model must outlive it and is
+ * only read. */
 typedef struct rgbd_server_config {
     int32_t n_slots;          /* device frame slots (frames in flight), 1..1024 */
     int32_t max_batch_faces;  /* faces per batch, 1..65536; a frame with more is rejected */
