@@ -228,3 +228,53 @@ def test_native_loop_edge_cases():
             assert torch.allclose(sc, ref, rtol=0, atol=5e-5 * float(np.abs(a).sum(1).max()))
     assert ref is not None and n > 0
     assert ctx.status() == 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dt,centred", [("fp8", False), ("bf16", True), ("f32", False)])
+def test_native_loop_model_types(dt, centred):
+    """The request loop scores with the model's own type (FP8 rows at the configured scale,
+    centred rows for a centred model, exact fp32): each frame's scores equal those of the C-ABI
+    calls made by hand on the same frame, within that type's parity tolerance."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1504_01883_gb300 import _build, serve
+    from paper_1504_01883_gb300 import binding as B
+    _build.build()
+    ctx = B.Context(0)
+    dim = 16 * 16 * 59
+    rng = synth.rng_for(95)
+    sv = synth.poisson_counts(rng, 300, dim)
+    a, b = synth.rbf_coefficients(rng, 10, 300)
+    model = B.svm_train_data_pack(ctx, torch.from_numpy(sv.view(np.int16)).cuda(), torch.from_numpy(a).cuda(),
+                                  torch.from_numpy(b).cuda(), gamma=1.0 / dim, dtype=dt, centred=centred)
+    streams = serve.make_streams(seed=12, n_streams=3, frames_per_stream=2)
+    H, W = streams[0].grey.shape[1:]
+    srv = B.NativeServer(model, H, W, n_streams=3, n_slots=4, max_batch_faces=64, x_scale=448.0)
+    scale = np.abs(a).sum(1)[None, :] + np.abs(b)[None, :]
+    bound = {"fp8": 1e-3, "bf16": 5e-5, "f32": 1e-5}[dt]
+    try:
+        for s_id, st in enumerate(streams):
+            for k in range(2):
+                g = torch.from_numpy(st.grey[k]).pin_memory()
+                d = torch.from_numpy(st.depth[k].view(np.int16)).pin_memory()
+                rr = np.ascontiguousarray(st.rects[k])
+                rects = torch.from_numpy(rr.view(np.int32).reshape(-1, 5))
+                sc = torch.empty((rects.shape[0], 10))
+                lb = torch.empty((rects.shape[0],), dtype=torch.int32)
+                rid = srv.submit(s_id, g, d, rects, sc, lb)
+                got = []
+                for _ in range(200):
+                    got += [c for c in srv.poll(wait_us=50000) if c[0] == rid]
+                    if got:
+                        break
+                assert got and got[0][1] == 0
+                _, x, q = B.lbp_fused_features(ctx, g.cuda()[None], d.cuda()[None], B.rects_tensor(rr), crop=128,
+                                               feats=False, x_dtype=dt, x_scale=448.0,
+                                               x_centre=model if centred else None)
+                want, _ = B.svm_score(ctx, model, x, q, x_scale=448.0)
+                assert np.max(np.abs(sc.numpy() - want.cpu().numpy()) / scale) <= bound
+    finally:
+        srv.close()
+    assert ctx.status() == 0
