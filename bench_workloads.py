@@ -423,16 +423,48 @@ def run_train(args):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     it = iters.cpu().numpy()
-    model = B.svm_train_data_pack(ctx, cnt, coef, bias, gamma=gamma, dtype="bf16")
-    xt, qt = B.lbp_normalize_features(ctx, torch.from_numpy(test.view(np.int16)).to(dev), "bf16")
-    _, pred = B.svm_score(ctx, model, xt, qt)
-    acc = float((pred.cpu().numpy() == test_lab).mean())
+    # the trained model scored in every precision on the held-out rows: label agreement with
+    # the exact fp32 path and with fp64 where the classes are structured (real margins), beside
+    # the precision workload's i.i.d. rows
+    import oracle as orc
+    orc.build()
+    tcnt = torch.from_numpy(test.view(np.int16)).to(dev)
+    a64 = coef.double().cpu().numpy()
+    b64 = bias.double().cpu().numpy()
+    x64 = orc.normalize_f64(test)
+    sv64 = orc.normalize_f64(counts)
+    d2 = (x64 * x64).sum(1)[:, None] + (sv64 * sv64).sum(1)[None, :] - 2.0 * (x64 @ sv64.T)
+    ref = np.exp(-gamma * np.maximum(d2, 0.0)) @ a64.T + b64[None, :]
+    ref_oracle = orc.svm_rbf(x64[:8], sv64, a64, b64, gamma)  # the BLAS expansion checked on 8 rows
+    ref_lab = orc.argmax(ref)
+    srt = np.sort(ref, axis=1)
+    margin = srt[:, -1] - srt[:, -2]
+    per_mode = {}
+    lab_f32 = None
+    for dt_base, centred in [("f32", False), ("bf16", False), ("bf16", True), ("fp8", False), ("fp8", True),
+                             ("tf32", False), ("bf16x3", False)]:
+        m = B.svm_train_data_pack(ctx, cnt, coef, bias, gamma=gamma, dtype=dt_base, centred=centred)
+        xt, qt = B.lbp_normalize_features(ctx, tcnt, dt_base, x_centre=m if centred else None)
+        s, pred = B.svm_score(ctx, m, xt, qt)
+        s = s.double().cpu().numpy()
+        pred = pred.cpu().numpy()
+        lab_f32 = pred if dt_base == "f32" else lab_f32
+        err = float(np.abs(s - ref).max())
+        per_mode[dt_base + ("_centred" if centred else "")] = {
+            "max_abs_err_vs_fp64": err, "label_agreement_vs_fp64": float((pred == ref_lab).mean()),
+            "label_agreement_vs_f32": float((pred == lab_f32).mean()),
+            "heldout_accuracy": float((pred == test_lab).mean()),
+            "rows_with_fp64_margin_above_2x_error": float((margin > 2.0 * err).mean())}
+        m.free()
     n_sv = int((coef.abs().amax(0) > 0).sum().item())
     return _emit({"workload": f"train: {C * per} rows ({C} classes x {per}), {dim}-dim per-cell normalised "
                               f"histograms, RBF gamma={gamma}, cost={cost}, SMO gap {eps}",
                   "metric": "training time (ms) for all one-vs-rest classifiers", "ms": float(np.median(ts)),
                   "smo_steps_per_class": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
-                  "support_vectors": n_sv, "heldout_accuracy_bf16_scoring": acc, "status": ctx.status(clear=True)})
+                  "support_vectors": n_sv, "heldout_rows": int(test.shape[0]),
+                  "fp64_blas_vs_oracle_max_abs": float(np.abs(ref[:8] - ref_oracle).max()),
+                  "fp64_margin_top1_top2": {"min": float(margin.min()), "median": float(np.median(margin))},
+                  "scoring_precision": per_mode, "status": ctx.status(clear=True)})
 
 
 def run(args):
