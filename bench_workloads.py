@@ -36,7 +36,7 @@ def _peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
 # ---------------------------------------------------------------------------------------------
@@ -205,7 +205,13 @@ def run_precision(args):
         x, q = B.lbp_normalize_features(ctx, X, dt_base, x_scale=x_scale, x_centre=model if centred else None)
         s_out, l_out = B.svm_score(ctx, model, x, q, x_scale=x_scale)
         torch.cuda.synchronize()
-        reps = 1 if dt == "f32" else 20  # ~0.2-1.3 s under load, long enough for the clock samples
+        t_first = time.perf_counter()
+        B.svm_score(ctx, model, x, q, x_scale=x_scale, scores=s_out, labels=l_out)
+        torch.cuda.synchronize()
+        ms0 = (time.perf_counter() - t_first) * 1e3
+        # >= ~1.5 s of back-to-back launches per tensor-core mode: the power cap settles and the
+        # 100 ms clock and power samples see it
+        reps = 1 if dt == "f32" else max(20, int(1500.0 / max(ms0, 1e-3)) + 1)
         ts = []
         clocks = bench.ClockSampler(0)
         clocks.start()
@@ -221,8 +227,12 @@ def run_precision(args):
         flops = 2.0 * n_rows * n_sv * dim + 2.0 * n_rows * n_sv * C
         ratio = {"bf16": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25, "bf16x3": 1.0 / 3.0}.get(dt_base)
         peak = pk["bf16_tflops"] * ratio if ratio else None
+        peak_s = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * ratio if ratio else None
+        # the modes run back to back for a second or more: the sustained (power-capped) peak is
+        # the one that applies; the burst fraction is kept beside it
         res[dt] = {"ms": ms, "tflops": flops / ms / 1e9, "frac_of_peak": (flops / ms / 1e9) / peak if peak else None,
-                   "peak_tflops": peak, "clocks": clk}
+                   "peak_tflops": peak, "frac_of_sustained_peak": (flops / ms / 1e9) / peak_s if peak_s else None,
+                   "sustained_peak_tflops": peak_s, "reps": reps, "clocks": clk}
         labels[dt] = l_out.cpu().numpy()
         sub_scores[dt] = s_out[:oracle_rows].cpu().numpy()
         if dt == "f32":
