@@ -406,8 +406,8 @@ int rgbd_track_streams(rgbd_ctx* ctx, rgbd_rect* state_rects, int32_t* state_ids
  *     RGBD_NOALLOC_SCRATCH_BYTES launches nothing and returns RGBD_ERR_ARG with
  *     the sizes in rgbd_last_error().
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, which may load the module); make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress, which may load the module and so take longer than
+ *     later calls); a latency-bound caller makes one warm-up call first.
  *   - Every call on a device shares the one array, which keeps the previous
  *     call's contents (each call overwrites what it reads).  Calls whose work
  *     overlaps on the GPU -- on different streams, or from different threads
