@@ -245,7 +245,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "crops/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * per_step / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(wl, "f64"),
+            "data": "synthetic",
+            "config": dict(workload_config(wl, "f64"), l2="not applicable: the oracle runs on the host cores",
+                           graph="none (host code)"),
             "cpu_baseline": {"value": v, "unit": "crops/s", "cores": 1, "kind": "oracle",
                              "sample": f"{per_step} faces per step of the 4096-face batch, single thread"},
             "e2e": {"value": v, "unit": "crops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
