@@ -10,7 +10,8 @@
 //                      one-frame workload, bound by reading the SV matrix once);
 //   rbf_tiled_kernel   128 x 128 register-tiled SGEMM over (rows, SVs), E in the epilogue,
 //                      then E x a^T accumulated per split.
-// reduce_scores_kernel adds the splits, asum and the bias, and takes the argmax.
+// reduce_scores_kernel adds the splits, asum and the bias, and takes the argmax
+// (reduce_scores_hoisted_kernel: the same with the row-independent sums shared by a block).
 #include <algorithm>
 
 #include "internal.h"
@@ -299,14 +300,88 @@ __global__ void reduce_scores_kernel(const float* __restrict__ part, const float
     }
 }
 
+// The same combination with the row-independent parts hoisted: a block of rows first sums, per
+// split and class, the coefficients of the split's tiles (sum_{i in split s} a_ci) and, per row
+// and split, delta_s = expm1(-gamma (r_s - r*)), into shared memory; then one warp per row adds
+// the splits in the same order and with the same operations as reduce_scores_kernel, so the
+// scores are bit-identical to it.  (reduce_scores_kernel repeats the tile sums per row and the
+// expm1 per class, as a chain of dependent loads in every warp.)
+__global__ void reduce_scores_hoisted_kernel(const float* __restrict__ part, const float* __restrict__ ref,
+                                             int splits, int n, int C, int C_stride,
+                                             const float* __restrict__ asum, const float* __restrict__ asum_tile,
+                                             int tps, int nt, const float* __restrict__ bias, float gamma,
+                                             float* __restrict__ scores, int32_t* __restrict__ labels) {
+    extern __shared__ float sh[];
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* s_as = sh;                              // [splits][C]
+    float* s_del = sh + (size_t)splits * C;        // [nw][splits]
+    const int row = blockIdx.x * nw + warp;
+    if (ref) {
+        for (int i = threadIdx.x; i < splits * C; i += blockDim.x) {
+            const int sp = i / C, c = i - sp * C;
+            float as = 0.f;
+            if (sp > 0)
+                for (int t = sp * tps; t < min(nt, (sp + 1) * tps); ++t) as += asum_tile[(size_t)t * C_stride + c];
+            s_as[i] = as;
+        }
+    }
+    float escale = 1.f;
+    if (ref && row < n) {
+        const float rstar = ref[row];
+        escale = expf(-gamma * rstar);
+        for (int sp = lane; sp < splits; sp += 32)
+            s_del[warp * splits + sp] = (sp == 0) ? 0.f : expm1f(-gamma * (ref[(size_t)sp * n + row] - rstar));
+    }
+    __syncthreads();
+    if (row >= n) return;
+    float best = -INFINITY;
+    int bi = 0x7FFFFFFF;
+    for (int c = lane; c < C; c += 32) {
+        float acc = 0.f;
+        for (int s = 0; s < splits; ++s) {
+            const float d = part[((size_t)s * n + row) * C_stride + c];
+            if (ref)
+                acc += d + s_del[warp * splits + s] * (s_as[s * C + c] + d);
+            else
+                acc += d;
+        }
+        const float sc = escale * (asum[c] + acc) + bias[c];
+        scores[(size_t)row * C + c] = sc;
+        if (sc > best) {
+            best = sc;
+            bi = c;
+        }
+    }
+    if (labels) {
+        for (int off = 16; off > 0; off >>= 1) {
+            const float ob = __shfl_xor_sync(FULL, best, off);
+            const int oi = __shfl_xor_sync(FULL, bi, off);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) labels[row] = bi;
+    }
+}
+
 }  // namespace
 
 int launch_reduce_scores(const float* part, const float* ref, int splits, int n, int C, int C_stride,
                          const float* asum, const float* asum_tile, int tiles_per_split, int n_tiles,
                          const float* bias, float gamma, float* scores, int32_t* labels, cudaStream_t s) {
-    const int rows_per_block = 8;
-    reduce_scores_kernel<<<(n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(
-        part, ref, splits, n, C, C_stride, asum, asum_tile, tiles_per_split, n_tiles, bias, gamma, scores, labels);
+    constexpr int kRowsHoisted = 16;
+    const size_t sh = sizeof(float) * ((size_t)splits * C + (size_t)kRowsHoisted * splits);
+    if (ref && sh <= 32 * 1024) {
+        reduce_scores_hoisted_kernel<<<(n + kRowsHoisted - 1) / kRowsHoisted, 32 * kRowsHoisted, sh, s>>>(
+            part, ref, splits, n, C, C_stride, asum, asum_tile, tiles_per_split, n_tiles, bias, gamma, scores,
+            labels);
+    } else {
+        const int rows_per_block = 8;
+        reduce_scores_kernel<<<(n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(
+            part, ref, splits, n, C, C_stride, asum, asum_tile, tiles_per_split, n_tiles, bias, gamma, scores,
+            labels);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "svm_score: reduce launch");
     return RGBD_OK;

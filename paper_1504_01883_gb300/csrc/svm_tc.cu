@@ -352,7 +352,7 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 // Split combine (A7), run by the last CTA of a 128-row block to finish: for each row and class
 //   S_c = exp(-gamma r*) (asum_c + sum_s [D_s + delta_s (asum_{c,s} + D_s)]) + b_c,
 // delta_s = expm1(-gamma (r_s - r*)), r* = r_0, asum_{c,s} the coefficient sum of split s's
-// tiles -- the same terms in the same order as reduce_scores_kernel -- then the argmax (lowest
+// tiles -- the same terms in the same order as the split-combine kernels of launch_reduce_scores -- then the argmax (lowest
 // class on ties).  The other splits' partial sums are read past L1 (__ldcg): their CTAs fenced
 // them before counting themselves finished.  `work` is shared memory of combine_bytes().
 // ---------------------------------------------------------------------------------------
@@ -1106,7 +1106,7 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     p.passes = pl.passes;
     // Small batches (up to 8 row blocks) combine their splits inside the kernel, in the last CTA
     // of each row block to finish, which saves a launch on the latency path of a serving batch;
-    // larger ones leave it to reduce_scores_kernel, which spreads the work over every SM instead
+    // larger ones leave it to the split-combine kernel, which spreads the work over every SM instead
     // of adding a tail to the last CTAs (on the 4096-row batch the fused combine cost ~9 us more).
     // The combine also needs its shared memory to fit the ring (every mode's holds >= 140 KB).
     p.fuse = (pl.mt <= 8 && combine_bytes(pl.splits, m->C_pad) <= (size_t)140 * 1024) ? 1 : 0;
