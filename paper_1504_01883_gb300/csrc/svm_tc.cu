@@ -352,8 +352,8 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 // Split combine (A7), run by the last CTA of a 128-row block to finish: for each row and class
 //   S_c = exp(-gamma r*) (asum_c + sum_s [D_s + delta_s (asum_{c,s} + D_s)]) + b_c,
 // delta_s = expm1(-gamma (r_s - r*)), r* = r_0, asum_{c,s} the coefficient sum of split s's
-// tiles -- the same terms in the same order as the split-combine kernels of launch_reduce_scores -- then the argmax (lowest
-// class on ties).  The other splits' partial sums are read past L1 (__ldcg): their CTAs fenced
+// tiles -- the same terms in the same order as the split-combine kernels of
+// launch_reduce_scores -- then the argmax (lowest class on ties).  The other splits' partial sums are read past L1 (__ldcg): their CTAs fenced
 // them before counting themselves finished.  `work` is shared memory of combine_bytes().
 // ---------------------------------------------------------------------------------------
 __host__ __device__ inline size_t combine_bytes(int splits, int C_pad) {
