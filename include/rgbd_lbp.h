@@ -143,11 +143,17 @@ int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear);
  *                               0 = default (3), 2 = no pairing, 3 = each pair runs one
  *                               256-row MMA (tcgen05 cta_group::2, each CTA holding half of
  *                               the SV tile)
- * Errors: RGBD_ERR_ARG for an unknown key, a negative value or a pairing other than 0, 2, 3. */
+ *   RGBD_TUNE_TC_SPLITK         tensor-core scoring of at most 128 rows: 0 = default (the K
+ *                               extent of every SV tile is split over several CTAs when the
+ *                               tiles alone would occupy fewer than half the SMs), 1 = never,
+ *                               k >= 2 = always, in k ranges (at most one per 8 k-blocks)
+ * Errors: RGBD_ERR_ARG for an unknown key, a negative value, a pairing other than 0, 2, 3 or
+ * more than 4096 K ranges. */
 #define RGBD_TUNE_LBP_CTAS_PER_SM 1
 #define RGBD_TUNE_TC_SPLITS 2
 #define RGBD_TUNE_TC_PAIRING 3
 #define RGBD_TUNE_LBP_SHAPE 4
+#define RGBD_TUNE_TC_SPLITK 5
 int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value);
 
 /* ======================================================================================= */

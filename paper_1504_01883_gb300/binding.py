@@ -24,7 +24,7 @@ DT_F32, DT_BF16, DT_FP8, DT_TF32, DT_BF16X3 = 1, 2, 3, 4, 5
 DT_CENTRED = 0x100  # svm_train_data_pack flag: SVs stored relative to their mean
 KERNEL_LINEAR, KERNEL_RBF = 0, 1
 LBP_GE, LBP_NBR_IGNORE_MASK, LBP_FACE_HIST256 = 1, 2, 4
-TUNE_LBP_CTAS_PER_SM, TUNE_TC_SPLITS, TUNE_TC_PAIRING, TUNE_LBP_SHAPE = 1, 2, 3, 4
+TUNE_LBP_CTAS_PER_SM, TUNE_TC_SPLITS, TUNE_TC_PAIRING, TUNE_LBP_SHAPE, TUNE_TC_SPLITK = 1, 2, 3, 4, 5
 STATUS_BAD_RECT, STATUS_WAIT_TIMEOUT = 1, 2
 NBINS, CELL = 59, 8
 

@@ -151,6 +151,10 @@ int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value) {
             CHECK_ARG(value <= 2, "rgbd_ctx_set_tuning: fused-kernel shape %d (0, 1 or 2)", value);
             ctx->tune_lbp_shape = value;
             return RGBD_OK;
+        case RGBD_TUNE_TC_SPLITK:
+            CHECK_ARG(value <= 4096, "rgbd_ctx_set_tuning: %d K ranges (at most 4096)", value);
+            ctx->tune_tc_splitk = value;
+            return RGBD_OK;
         case RGBD_TUNE_TC_PAIRING:
             CHECK_ARG(value == 0 || value == 2 || value == 3, "rgbd_ctx_set_tuning: CTA pairing %d (0, 2 or 3)", value);
             ctx->tune_tc_pairing = value;

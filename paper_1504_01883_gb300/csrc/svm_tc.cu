@@ -907,6 +907,340 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Small batches (one 128-row block): split over K.
+// ---------------------------------------------------------------------------------------
+// With at most 128 rows the kernel above runs one CTA per SV tile at most (32 CTAs for 8192
+// SVs), and each streams a whole 7.7 MB SV tile through its ring: a one-frame serving batch
+// takes as long as 4096 rows take per CTA.  Here the K extent (the k-blocks of every pass) of
+// each SV tile is cut into `kz` ranges, one CTA per (tile, range), so that all SMs stream the
+// SVs; each CTA writes its partial G = X . SV_t^T of the valid rows to `gpart`
+// ([kz][n_pad][n]), and rbf_splitk_epilogue_kernel adds the ranges, finishes the tile and, in
+// the last CTA of each row group, combines the tiles into scores and labels.
+// Warps: 0 the TMA producer (4 stages of X and SV k-blocks), 1 the TMEM owner and MMA issuer,
+// 2-5 the epilogue (one thread per row, TMEM lane quarter = warp % 4).  The X copies hold only
+// the batch's rows (rounded up to 8, the swizzle atom's height): the MMA still reads 128 rows,
+// but an output row depends only on its own A row, and rows past the batch are never written.
+// G for one SV tile lives in 256 tensor-memory columns.
+constexpr int SK_WARPS = 6;
+constexpr int SK_STAGES = 4;
+constexpr int SK_STAGE = X_TILE + SV_TILE;
+constexpr int SK_BAR_OFF = SK_STAGES * SK_STAGE;
+constexpr int SK_SMEM = SK_BAR_OFF + 256 + 1024;
+enum { SK_FULL = 0, SK_EMPTY = SK_FULL + SK_STAGES, SK_GFULL = SK_EMPTY + SK_STAGES, SK_DRAIN = SK_GFULL + 1,
+       SK_COUNT = SK_DRAIN + 1 };
+
+struct SkParams {
+    int n;          // rows (<= BM)
+    int n_pad;      // SV rows of the model (a multiple of BN)
+    int k_blocks;   // k-blocks per pass
+    int k_elems;    // elements per k-block
+    int passes;     // 1, or 3 for split bf16 operands
+    int kpz;        // k-blocks (over all passes) per K range
+    uint32_t x_bytes;  // bytes of one X k-block: only the valid rows, rounded up to 8, are copied
+    uint32_t idesc;
+    float* gpart;   // [kz][n_pad][n]
+    uint32_t* counters;  // [n_groups]: finished tiles per row group of the epilogue, zeroed here
+    int n_groups;
+    uint32_t* status;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(SK_WARPS * 32, 1)
+    rbf_tc_splitk_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_sv,
+                         const __grid_constant__ CUtensorMap tm_x2, const __grid_constant__ CUtensorMap tm_sv2,
+                         const SkParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - raw);
+    const uint32_t bars = base + SK_BAR_OFF;
+    auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + SK_BAR_OFF + 8 * SK_COUNT);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + SK_BAR_OFF + 8 * SK_COUNT + 8);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x, z = blockIdx.y;
+    const int KT = p.passes * p.k_blocks;
+    const int kt0 = z * p.kpz, kt1 = min(KT, kt0 + p.kpz);  // non-empty: the host sizes kz so
+
+    if (blockIdx.x == 0 && blockIdx.y == 0)  // the epilogue kernel that follows counts on these
+        for (int i = threadIdx.x; i < p.n_groups; i += blockDim.x) p.counters[i] = 0u;
+    // the epilogue kernel may be scheduled now: its CTAs wait (griddepcontrol.wait) for this grid
+    // to complete, so its launch latency hides behind this kernel instead of following it
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SK_STAGES; ++s) {
+            bar_init(bar(SK_FULL + s), 1);
+            bar_init(bar(SK_EMPTY + s), 1);
+        }
+        bar_init(bar(SK_GFULL), 1);
+        bar_init(bar(SK_DRAIN), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ===================== TMA producer =====================
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0, armed = 0, armed_par = 0;
+            for (int kt = kt0; kt < kt1; ++kt) {
+                const int pass = kt / p.k_blocks, kb = kt - pass * p.k_blocks;
+                const CUtensorMap* mx = (pass == 2) ? &tm_x2 : &tm_x;
+                const CUtensorMap* msv = (pass == 1) ? &tm_sv2 : &tm_sv;
+                if (!bar_spin<false>(bar(SK_EMPTY + stage), phase ^ 1u, abort_flag, p.status)) break;
+                const uint32_t sa = base + (uint32_t)stage * SK_STAGE;
+                bar_arrive_tx(bar(SK_FULL + stage), p.x_bytes + SV_TILE);
+                tma_load_2d(sa, mx, kb * p.k_elems, 0, bar(SK_FULL + stage));
+                tma_load_2d(sa + X_TILE, msv, kb * p.k_elems, tile * BN, bar(SK_FULL + stage));
+                armed |= 1u << stage;
+                armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+                if (++stage == SK_STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            if (*abort_flag) {  // drain: wait (bounded) for the copies this thread issued
+                const uint64_t tq = globaltimer();
+                for (int s = 0; s < SK_STAGES; ++s)
+                    if (armed & (1u << s))
+                        while (!bar_try(bar(SK_FULL + s), (armed_par >> s) & 1u) && globaltimer() - tq < WAIT_NS) {
+                        }
+            }
+        }
+    } else if (warp == 1) {
+        // ===================== MMA issuer =====================
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool alive = true;
+            for (int kt = kt0; kt < kt1; ++kt) {
+                if (!bar_try(bar(SK_FULL + stage), phase) &&
+                    !bar_wait<false, true>(bar(SK_FULL + stage), phase, abort_flag, p.status)) {
+                    alive = false;
+                    break;
+                }
+                const uint32_t sa = base + (uint32_t)stage * SK_STAGE;
+                const uint64_t a0 = sdesc(sa), b0 = sdesc(sa + X_TILE);
+                mma_issue<1, KIND>(tmem, a0, b0, p.idesc, kt > kt0 ? 1u : 0u);
+#pragma unroll
+                for (int ks = 1; ks < 4; ++ks) mma_issue<1, KIND>(tmem, a0 + 2u * ks, b0 + 2u * ks, p.idesc, 1u);
+                tc_commit(bar(SK_EMPTY + stage));
+                if (++stage == SK_STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            if (alive) tc_commit(bar(SK_GFULL));
+            // drain: every MMA this thread issued has completed once SK_DRAIN flips
+            tc_commit(bar(SK_DRAIN));
+            const uint64_t tq = globaltimer();
+            while (!bar_try(bar(SK_DRAIN), 0)) {
+                if (globaltimer() - tq > WAIT_NS) break;
+            }
+        }
+    } else {
+        // ===================== epilogue: warps 2..5, one thread per row =====================
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        bool ok = false;
+        if (lane == 0) ok = bar_wait<false>(bar(SK_GFULL), 0, abort_flag, p.status);
+        if (__shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0)) {
+            tc_fence_after();
+            const uint32_t g_tmem = tmem + ((uint32_t)(quarter * 32) << 16);
+            float* out = p.gpart + ((size_t)z * p.n_pad + (size_t)tile * BN) * p.n + row;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t v[32];
+                TC_LD_X32(g_tmem + c, v);
+                tc_wait_ld();
+                if (row < p.n) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) out[(size_t)(c + j) * p.n] = __uint_as_float(v[j]);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+                     : "memory");
+    }
+}
+
+// Finishes one SV tile for up to SKE_ROWS rows: G = the sum of the K ranges' partials,
+// d^2 = |x|^2 + |sv|^2 - 2 G, the row's reference distance r (mean d^2 over the tile's real SVs),
+// F = expm1(-gamma (d^2 - r)) and D_c = sum_i a_ci F_i with the fp32 coefficients.  Each tile
+// is one split of the split combine (D and r per tile); the last CTA of a row group to finish
+// (counters[row group], zeroed by the split-K kernel) adds the tiles of its rows and takes the
+// argmax, with the terms of the combine kernels of launch_reduce_scores.  The loads of each step
+// are issued together: the kernel is a short chain of dependent L2 round trips.
+constexpr int SKE_ROWS = 16;
+constexpr int SKE_THREADS = 256;
+constexpr int SKE_CPW = 4;  // classes per warp and pass (their coefficients loaded at once)
+__global__ void __launch_bounds__(SKE_THREADS) rbf_splitk_epilogue_kernel(
+    const float* __restrict__ gpart, int kz, int n_pad, int n, const float* __restrict__ xsq,
+    const float* __restrict__ svsq, int n_sv, const float* __restrict__ coef, int C, int C_pad, float gamma,
+    float gscale, float* __restrict__ part, float* __restrict__ ref, uint32_t* __restrict__ counters, int nt,
+    const float* __restrict__ asum, const float* __restrict__ asum_tile, const float* __restrict__ bias,
+    float* __restrict__ scores, int32_t* __restrict__ labels) {
+    __shared__ float F[SKE_ROWS][BN];
+    __shared__ float r_row[SKE_ROWS];
+    __shared__ int last;
+    // launched as a programmatic dependent of the split-K kernel: wait for it to complete
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int tile = blockIdx.x, k0 = blockIdx.y * SKE_ROWS;
+    const int rows = min(SKE_ROWS, n - k0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = SKE_THREADS / 32;
+    static_assert(SKE_THREADS == BN, "one thread per SV column of the tile");
+    {
+        // thread = column: every K range's partial of every row, all loads issued together
+        const int col = tile * BN + threadIdx.x;
+        const size_t zs = (size_t)n_pad * n;
+        const float* gp = gpart + (size_t)col * n + k0;
+        float g[SKE_ROWS];
+#pragma unroll
+        for (int k = 0; k < SKE_ROWS; ++k) g[k] = 0.f;
+        for (int zz = 0; zz < kz; ++zz) {
+#pragma unroll
+            for (int k = 0; k < SKE_ROWS; ++k)
+                if (k < rows) g[k] += gp[zz * zs + k];
+        }
+        const bool real = col < n_sv;
+        const float svs = real ? svsq[col] : 0.f;
+#pragma unroll
+        for (int k = 0; k < SKE_ROWS; ++k)
+            if (k < rows) F[k][threadIdx.x] = real ? xsq[k0 + k] + svs - 2.f * gscale * g[k] : 0.f;
+    }
+    __syncthreads();
+    const int valid = min(BN, n_sv - tile * BN);
+    for (int k = warp; k < rows; k += nw) {
+        float sum = 0.f;
+        for (int i = lane; i < valid; i += 32) sum += F[k][i];
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
+        if (lane == 0) r_row[k] = sum / (float)max(valid, 1);
+    }
+    __syncthreads();
+    for (int k = 0; k < rows; ++k) {
+        const int i = threadIdx.x;
+        F[k][i] = i < valid ? expm1_near0(-gamma * (F[k][i] - r_row[k])) : 0.f;
+    }
+    __syncthreads();
+    for (int c0 = warp * SKE_CPW; c0 < C; c0 += nw * SKE_CPW) {
+        float a[SKE_CPW][BN / 32];
+#pragma unroll
+        for (int cc = 0; cc < SKE_CPW; ++cc)
+#pragma unroll
+            for (int j = 0; j < BN / 32; ++j)
+                a[cc][j] = c0 + cc < C ? coef[(size_t)(c0 + cc) * n_pad + tile * BN + lane + 32 * j] : 0.f;
+        for (int k = 0; k < rows; ++k) {
+            float sk[SKE_CPW];
+#pragma unroll
+            for (int cc = 0; cc < SKE_CPW; ++cc) {
+                float t = 0.f;
+#pragma unroll
+                for (int j = 0; j < BN / 32; ++j) t = fmaf(F[k][lane + 32 * j], a[cc][j], t);
+                sk[cc] = t;
+            }
+#pragma unroll
+            for (int cc = 0; cc < SKE_CPW; ++cc)
+                for (int off = 16; off > 0; off >>= 1) sk[cc] += __shfl_xor_sync(0xFFFFFFFFu, sk[cc], off);
+            if (lane < SKE_CPW && c0 + lane < C) {
+                float v = sk[0];
+#pragma unroll
+                for (int cc = 1; cc < SKE_CPW; ++cc) v = lane == cc ? sk[cc] : v;
+                part[((size_t)tile * n + k0 + k) * C_pad + c0 + lane] = v;
+            }
+        }
+    }
+    if (threadIdx.x < rows) ref[(size_t)tile * n + k0 + threadIdx.x] = r_row[threadIdx.x];
+
+    // ---- the last tile of this row group to finish adds the tiles ----
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counters + blockIdx.y, 1u) == (uint32_t)nt - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // shared memory (F reused): delta_s per row and tile, the tiles' coefficient sums when they
+    // fit, then the scores of the group's rows
+    float* s_del = &F[0][0];                       // [rows][nt] (nt <= 256)
+    float* s_as = s_del + rows * nt;               // [nt][C] or unused
+    const bool as_fit = rows * nt + nt * C + rows * C <= SKE_ROWS * BN;
+    float* s_sc = as_fit ? s_as + nt * C : s_del + rows * nt;  // [rows][C]
+    const bool sc_fit = (int)(s_sc - s_del) + rows * C <= SKE_ROWS * BN;
+    for (int idx = threadIdx.x; idx < rows * nt; idx += SKE_THREADS) {
+        const int k = idx / nt, t = idx - k * nt;
+        s_del[idx] = t == 0 ? 0.f : expm1f(-gamma * (__ldcg(ref + (size_t)t * n + k0 + k) - __ldcg(ref + k0 + k)));
+    }
+    if (as_fit)
+        for (int idx = threadIdx.x; idx < nt * C; idx += SKE_THREADS) {
+            const int t = idx / C, c = idx - t * C;
+            s_as[idx] = t == 0 ? 0.f : __ldg(asum_tile + (size_t)t * C_pad + c);
+        }
+    __syncthreads();
+    // thread = (row, class): the tiles' partial sums loaded 16 at a time, then added in tile order
+    for (int idx = threadIdx.x; idx < rows * C; idx += SKE_THREADS) {
+        const int k = idx / C, c = idx - k * C;
+        const float* pp = part + (size_t)(k0 + k) * C_pad + c;
+        const size_t ts = (size_t)n * C_pad;
+        float acc = 0.f;
+        for (int t0 = 0; t0 < nt; t0 += 16) {
+            float d[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) d[j] = t0 + j < nt ? __ldcg(pp + (t0 + j) * ts) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (t0 + j < nt) {
+                    const int t = t0 + j;
+                    const float as = as_fit ? s_as[t * C + c] : (t == 0 ? 0.f : __ldg(asum_tile + (size_t)t * C_pad + c));
+                    acc += d[j] + s_del[k * nt + t] * (as + d[j]);
+                }
+            }
+        }
+        const float sc = expf(-gamma * __ldcg(ref + k0 + k)) * (__ldg(asum + c) + acc) + __ldg(bias + c);
+        scores[(size_t)(k0 + k) * C + c] = sc;
+        if (sc_fit) s_sc[idx] = sc;
+    }
+    if (!labels) return;
+    __syncthreads();
+    for (int k = warp; k < rows; k += nw) {
+        float best = -INFINITY;
+        int bi = 0x7FFFFFFF;
+        for (int c = lane; c < C; c += 32) {
+            const float v = sc_fit ? s_sc[k * C + c] : __ldcg(scores + (size_t)(k0 + k) * C + c);
+            if (v > best) {
+                best = v;
+                bi = c;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const float ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+            const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, off);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) labels[k0 + k] = bi;
+    }
+}
+
 // Number of SV-tile ranges ("splits") per 128-row block.  One CTA runs per SM, so the time
 // is about waves x (tiles per CTA + 1): the +1 stands for the pipeline fill, the epilogue of
 // the last tile and the partial-sum write that every CTA pays once.  Fewer splits win ties.
@@ -995,12 +1329,14 @@ namespace {
 
 struct TcPlan {
     int esz, kind, passes, splits, tps, mt, nt;
+    int kz, kpz;  // K ranges of the small-batch path (0: the tile kernel) and k-blocks per range
     uint32_t fmt;
     CUtensorMapDataType dt;
-    size_t off_ref, off_cnt, bytes;
+    size_t off_ref, off_cnt, off_gpart, bytes;  // (the small-batch path keeps its counters at off_cnt)
 };
 
-int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
+// ws_cap: the scratch a caller can offer; the small-batch path is planned only if it fits.
+int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl, size_t ws_cap = ~size_t(0)) {
     if (m->C > MAX_CPAD || !m->has_tmaps)
         return set_error(RGBD_ERR_UNSUPPORTED, "svm_score: tensor-core RBF supports up to %d classes", MAX_CPAD);
     if (ctx->props.cc_major != 10)
@@ -1024,6 +1360,34 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
     if (m->dtype == RGBD_DT_BF16X3) pl->kind = 3;  // split bf16, second product split too
     pl->mt = (n + BM - 1) / BM;
     pl->nt = m->n_pad / BN;
+    // One 128-row block whose SV tiles cannot occupy half the SMs: split K instead (tuning value
+    // 1 turns this off, >= 2 forces that many K ranges); every range holds >= 8 k-blocks.
+    pl->kz = 0;
+    pl->kpz = 0;
+    if (pl->mt == 1 && pl->nt <= 256 && ctx->tune_tc_splitk != 1) {
+        const int KT = pl->passes * (m->k_pad * pl->esz / 128);
+        int kz = ctx->tune_tc_splitk >= 2 ? ctx->tune_tc_splitk
+                                          : (2 * pl->nt <= ctx->props.sm_count ? ctx->props.sm_count / pl->nt : 0);
+        kz = std::min(kz, std::max(1, KT / 8));
+        if (kz >= 2) {
+            pl->kpz = (KT + kz - 1) / kz;
+            pl->kz = (KT + pl->kpz - 1) / pl->kpz;  // every range non-empty
+            if (pl->kz < 2) pl->kz = 0;
+        }
+    }
+    if (pl->kz) {
+        // each SV tile is one split of the combine
+        pl->splits = pl->nt;
+        pl->tps = 1;
+        const size_t part_bytes = sizeof(float) * (size_t)pl->nt * n * m->C_pad;
+        const size_t ref_bytes = sizeof(float) * (size_t)pl->nt * n;
+        pl->off_ref = (part_bytes + 255) & ~size_t(255);
+        pl->off_cnt = (pl->off_ref + ref_bytes + 255) & ~size_t(255);
+        pl->off_gpart = pl->off_cnt + 256;  // counters: one per group of SKE_ROWS rows (<= 8)
+        pl->bytes = pl->off_gpart + sizeof(float) * (size_t)pl->kz * m->n_pad * n;
+        if (pl->bytes <= ws_cap) return RGBD_OK;
+        pl->kz = 0;  // too large for the caller's scratch: the tile kernel instead
+    }
     pl->splits = ctx->tune_tc_splits > 0 ? std::min(ctx->tune_tc_splits, pl->nt)
                                          : choose_splits(pl->mt, pl->nt, ctx->props.sm_count);
     pl->tps = (pl->nt + pl->splits - 1) / pl->splits;
@@ -1033,7 +1397,20 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl) {
     pl->off_ref = (part_bytes + 255) & ~size_t(255);
     pl->off_cnt = (pl->off_ref + ref_bytes + 255) & ~size_t(255);
     pl->bytes = pl->off_cnt + sizeof(uint32_t) * (size_t)((pl->mt + 1) / 2 * 2);  // one counter per row block
+    pl->off_gpart = 0;
     return RGBD_OK;
+}
+
+// The small-batch path: K-range partials of G, their per-tile epilogue, the split combine.
+template <int KIND>
+cudaError_t launch_splitk(const TcPlan& pl, const SkParams& sp, const rgbd_svm* m, const CUtensorMap& tm_x,
+                          const CUtensorMap& tm_x2, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(rbf_tc_splitk_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SK_SMEM);
+    if (e != cudaSuccess) return e;
+    rbf_tc_splitk_kernel<KIND><<<dim3((unsigned)pl.nt, (unsigned)pl.kz), SK_WARPS * 32, SK_SMEM, s>>>(
+        tm_x, m->tm_sv, tm_x2, m->tm_sv_lo, sp);
+    return cudaGetLastError();
 }
 
 // Launches one instantiation: single CTAs on a (row blocks, splits) grid, pairs as clusters of
@@ -1072,14 +1449,56 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     float* part = (float*)ws;
     float* ref = (float*)(ws + pl.off_ref);
     CUtensorMap tm_x, tm_x2;
+    const float gscale = (m->dtype == RGBD_DT_FP8) ? 1.0f / (x_scale * m->sv_scale) : 1.0f;
+    // the small-batch path copies only the batch's rows of X (a multiple of 8)
+    const uint32_t x_rows = pl.kz ? (uint32_t)std::min(BM, (n + 7) & ~7) : (uint32_t)BM;
     int rc = encode_tmap_2d(&tm_x, pl.dt, x, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * pl.esz,
-                            128u / pl.esz, BM, CU_TENSOR_MAP_SWIZZLE_128B);
+                            128u / pl.esz, x_rows, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
     const void* x_lo = x;  // split bf16: the lo plane of the rows follows their hi plane
     if (pl.passes == 3) x_lo = reinterpret_cast<const uint16_t*>(x) + (size_t)n * m->k_pad;
     rc = encode_tmap_2d(&tm_x2, pl.dt, x_lo, (uint64_t)m->k_pad, (uint64_t)n, (uint64_t)m->k_pad * pl.esz,
-                        128u / pl.esz, BM, CU_TENSOR_MAP_SWIZZLE_128B);
+                        128u / pl.esz, x_rows, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
+    if (pl.kz) {
+        SkParams sp;
+        sp.n = n;
+        sp.n_pad = m->n_pad;
+        sp.k_blocks = m->k_pad * pl.esz / 128;
+        sp.k_elems = 128 / pl.esz;
+        sp.passes = pl.passes;
+        sp.kpz = pl.kpz;
+        sp.x_bytes = x_rows * 128u;
+        sp.idesc = make_idesc(pl.fmt, pl.fmt, BM, BN);
+        sp.gpart = (float*)(ws + pl.off_gpart);
+        sp.counters = reinterpret_cast<uint32_t*>(ws + pl.off_cnt);
+        sp.n_groups = (n + SKE_ROWS - 1) / SKE_ROWS;
+        sp.status = ctx->d_status;
+        cudaError_t e;
+        switch (pl.kind) {
+            case 0: e = launch_splitk<0>(pl, sp, m, tm_x, tm_x2, s); break;
+            case 1: e = launch_splitk<1>(pl, sp, m, tm_x, tm_x2, s); break;
+            case 2: e = launch_splitk<2>(pl, sp, m, tm_x, tm_x2, s); break;
+            default: e = launch_splitk<3>(pl, sp, m, tm_x, tm_x2, s); break;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "svm_score: split-K launch");
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)pl.nt, (unsigned)sp.n_groups, 1);
+        cfg.blockDim = dim3(SKE_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, rbf_splitk_epilogue_kernel, (const float*)sp.gpart, pl.kz, m->n_pad, n, xsq,
+                               (const float*)m->sv_sq, m->n_sv, (const float*)m->coef, m->C, m->C_pad, m->gamma,
+                               gscale, part, ref, sp.counters, pl.nt, (const float*)m->asum,
+                               (const float*)m->asum_tile, (const float*)m->bias, scores, labels);
+        if (e != cudaSuccess) return cuda_error(e, "svm_score: split-K epilogue launch");
+        return RGBD_OK;
+    }
     // Mode: tuning value 2 = single CTAs, 3 = 2-CTA MMA pairs, 0 = auto (the 2-CTA pairs).
     // Pairs need at least two 128-row blocks.
     int mode = MODE_SINGLE;
@@ -1094,7 +1513,7 @@ int launch_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq,
     p.tiles_per_split = pl.tps;
     p.n_tiles = pl.nt;
     p.gamma = m->gamma;
-    p.gscale = (m->dtype == RGBD_DT_FP8) ? 1.0f / (x_scale * m->sv_scale) : 1.0f;
+    p.gscale = gscale;
     p.xsq = xsq;
     p.svsq = m->sv_sq;
     p.part = part;
@@ -1172,7 +1591,7 @@ int score_rbf_tc_external_ws(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, co
                              float x_scale, float* scores, int32_t* labels, cudaStream_t s, void* ws_ptr,
                              size_t ws_cap, size_t* need) {
     TcPlan pl;
-    int rc = plan_tc(ctx, m, n, &pl);
+    int rc = plan_tc(ctx, m, n, &pl, ws_cap);
     if (rc) return rc;
     if (need) *need = pl.bytes;
     if (pl.bytes > ws_cap)

@@ -459,6 +459,39 @@ def test_tuning_changes_layout_not_results(B, ctx, orc, splits, mc):
     assert rel_score_error(s1.cpu().numpy(), s0.cpu().numpy().astype(np.float64), scale) <= 1e-5
 
 
+@pytest.mark.parametrize("dt,n,kz", [("bf16", 1, 0), ("bf16", 6, 0), ("bf16", 100, 0), ("bf16", 128, 0),
+                                     ("bf16", 37, 3), ("bf16", 5, 59), ("fp8", 12, 0), ("tf32", 9, 5),
+                                     ("bf16x3", 17, 4)])
+def test_small_batch_split_k(B, ctx, orc, dt, n, kz):
+    """Batches of one 128-row block split the K extent of every SV tile over several CTAs
+    (automatically when the tiles alone fill few SMs; kz forces that many ranges): scores
+    within the path's tolerance of the fp64 oracle, labels equal where the margin allows, and
+    the same scores as the tile kernel within rounding."""
+    # 8 SV tiles, the last ragged; 64 cells: 30 FP8 k-blocks, so even FP8 has 3 K ranges
+    X, SV, a, b, gamma = _scoring_problem(300 + n + kz, n, 2000, 24, cells=64)
+    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype=dt)
+    x, q = B.lbp_normalize_features(ctx, dev_u16(X), dt, x_scale=448.0)
+    ctx.set_tuning(B.TUNE_TC_SPLITK, kz)
+    try:
+        s, lab = B.svm_score(ctx, model, x, q, x_scale=448.0)
+        assert ctx.status() == 0
+        ctx.set_tuning(B.TUNE_TC_SPLITK, 1)  # the tile kernel, for comparison
+        s_tile, _ = B.svm_score(ctx, model, x, q, x_scale=448.0)
+    finally:
+        ctx.set_tuning(B.TUNE_TC_SPLITK, 0)
+    x64, sv64 = orc.normalize_f64(X), orc.normalize_f64(SV)
+    ref = orc.svm_rbf(x64, sv64, a, b, gamma)
+    scale = rbf_error_scale(x64, sv64, a, b, gamma)
+    err = rel_score_error(s.cpu().numpy(), ref, scale)
+    bound = {"tf32": 2e-5, "bf16": 5e-5, "fp8": 1e-3, "bf16x3": 1e-8}[dt]
+    print(f"{dt} n {n} kz {kz}: rel err {err:.3e}")
+    assert err <= bound, err
+    assert rel_score_error(s.cpu().numpy(), s_tile.cpu().numpy().astype(np.float64), scale) <= 2 * bound
+    srt = np.sort(ref, axis=1)
+    clear = (srt[:, -1] - srt[:, -2]) > 4 * bound * scale.max()
+    assert (lab.cpu().numpy()[clear] == orc.argmax(ref)[clear]).all()
+
+
 # ---------------------------------------------------------------------------------------------
 # Section 3's 0-255 face histogram and Section 2.3's nearest-centre tracking
 # ---------------------------------------------------------------------------------------------
