@@ -508,6 +508,19 @@ def main():
     e2e_ms = evs[0].elapsed_time(evs[1]) / e2e_steps
     h2d = h_grey.numel() + 2 * h_depth.numel() + 4 * h_rects.numel()
     d2h = 4 * h_scores.numel() + 4 * h_labels.numel()
+    # the host link's rate at this moment: one step's upload alone, on the same two streams
+    # (the end-to-end step cannot beat h2d bytes / this rate)
+    link_ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(up[0])
+        up[1].wait_event(e0)
+        upload(0)
+        up[0].wait_event(uploaded[0][1])
+        e1.record(up[0])
+        torch.cuda.synchronize()
+        link_ms.append(e0.elapsed_time(e1))
+    h2d_gbs = h2d / (min(link_ms) * 1e-3) / 1e9
 
     # ---- roofline of the dominant kernel --------------------------------------------------
     pk, src = peaks()
@@ -546,7 +559,8 @@ def main():
             "data": "synthetic", "config": workload_config(wl, dt),
             "roofline": roofline, "stages": {"k1": rl_k1, "k2": rl_k2},
             "e2e": {"value": round(world * n / (e2e_ms * 1e-3), 1), "unit": "crops/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),
+                    "h2d_gbs_alone": round(h2d_gbs, 1)},
             "gpu_launches": launches_per_step * args.steps, "clocks": clk, "device_status": status,
             "autotune": {"tuning": tune_report["tuning"], "timed_ms": tune_report["report"]}}
     line["config"]["l2"] = ("headline steps: each step's inputs exceed L2 (frames 236 MB, support vectors 124 MB, "

@@ -336,6 +336,11 @@ def serving_leg(ctx, seconds, warm_frames=50):
             cap, _ = srv.run(events, realtime=False)
             out[name]["capacity_crops_per_s"] = round(cap.crops / cap.wall_s, 1)
             out[name]["capacity_batches"] = cap.batches
+            if cap.submit_s:
+                # the caller's submission of the queued frames: when it takes most of the wall
+                # time, the capacity figure is the submitting thread's rate, not the GPU's
+                out[name]["capacity_submit_s"] = round(cap.submit_s, 4)
+                out[name]["capacity_wall_s"] = round(cap.wall_s, 4)
         if hasattr(srv, "close"):
             srv.close()
         del srv

@@ -147,6 +147,9 @@ int score_linear(rgbd_ctx* ctx, const rgbd_svm* m, const float* x, int n, float*
                  int32_t* labels, cudaStream_t s);
 int score_rbf_f32(rgbd_ctx* ctx, const rgbd_svm* m, const float* x, const float* xsq, int n,
                   float* scores, int32_t* labels, cudaStream_t s);
+// Workspace bytes a scoring call of n rows takes (0: none, or a model the path rejects).
+size_t score_rbf_f32_bytes(rgbd_ctx* ctx, const rgbd_svm* m, int n);
+size_t score_rbf_tc_bytes(rgbd_ctx* ctx, const rgbd_svm* m, int n);
 int score_rbf_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n,
                  float x_scale, float* scores, int32_t* labels, cudaStream_t s);
 

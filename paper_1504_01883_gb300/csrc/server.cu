@@ -404,6 +404,20 @@ int rgbd_server_create(const rgbd_svm* model, const rgbd_server_config* cfg, rgb
         free_server(s);
         return rc;
     }
+    if (e == cudaSuccess && model->kernel == RGBD_KERNEL_RBF) {
+        // the scoring workspace of the largest batch of either scoring path (at most 128 rows
+        // split over K, more rows by SV tiles), reserved now: growing it during serving would
+        // put a cudaFree / cudaMalloc pair, which wait for the device, in a frame's latency
+        size_t ws = 0;
+        for (int nq : {std::min(128, c.max_batch_faces), c.max_batch_faces})
+            ws = std::max(ws, model->dtype == RGBD_DT_F32 ? rgbd::score_rbf_f32_bytes(s->ctx, model, nq)
+                                                           : rgbd::score_rbf_tc_bytes(s->ctx, model, nq));
+        rc = ws ? rgbd::ensure_workspace(s->ctx, ws, nullptr) : RGBD_OK;
+        if (rc) {
+            free_server(s);
+            return rc;
+        }
+    }
     for (int i = c.n_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->frame_bytes = 3 * plane;
     s->face_bytes = x_elem_bytes(s->x_dtype) * (size_t)s->k_pad + sizeof(float) * (1 + (size_t)s->C) +

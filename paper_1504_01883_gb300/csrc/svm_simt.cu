@@ -403,6 +403,22 @@ static void launch_smallm(int blocks, cudaStream_t s, const float* x, const floa
                                                      m->n_sv, m->coef, m->n_pad, m->C, m->gamma, spw, part);
 }
 
+// The workspace score_rbf_f32 takes for n rows (the same arithmetic as its two paths).
+size_t score_rbf_f32_bytes(rgbd_ctx* ctx, const rgbd_svm* m, int n) {
+    if (n <= 8) {
+        const int warps_target = ctx->props.sm_count * 8 * 4;
+        const int spw = std::max(1, (m->n_sv + warps_target - 1) / warps_target);
+        const int nwarps = (m->n_sv + spw - 1) / spw;
+        return sizeof(float) * (size_t)((nwarps + 7) / 8 * 8) * n * m->C;
+    }
+    const int mt = (n + TBM - 1) / TBM;
+    const int nt = m->n_pad / TBN;
+    int splits = std::max(1, std::min(nt, (ctx->props.sm_count + mt - 1) / mt));
+    const int tps = (nt + splits - 1) / splits;
+    splits = (nt + tps - 1) / tps;
+    return sizeof(float) * (size_t)splits * n * m->C;
+}
+
 int score_rbf_f32(rgbd_ctx* ctx, const rgbd_svm* m, const float* x, const float* xsq, int n,
                   float* scores, int32_t* labels, cudaStream_t s) {
     if (m->C > 128) return set_error(RGBD_ERR_UNSUPPORTED, "svm_score: fp32 RBF supports up to 128 classes");

@@ -24,6 +24,9 @@
 // the epilogue overlap the next tile's main loop.  Partial sums D_s and r_s go to workspace;
 // launch_reduce_scores combines the splits.
 //
+// Batches of one 128-row block whose SV tiles would fill few SMs take rbf_tc_splitk_kernel
+// instead (the K extent of every tile split over several CTAs; see there).
+//
 // Every wait on an mbarrier is bounded by a %globaltimer deadline; on expiry the CTA sets
 // RGBD_STATUS_WAIT_TIMEOUT, stops issuing work, waits (bounded) for its own copies and MMAs
 // in flight, frees its tensor memory and returns.
@@ -1585,6 +1588,11 @@ int score_rbf_tc(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* x
     rc = ensure_workspace(ctx, pl.bytes, s);
     if (rc) return rc;
     return launch_tc(ctx, m, x, xsq, n, x_scale, scores, labels, s, pl, (char*)ctx->workspace);
+}
+
+size_t score_rbf_tc_bytes(rgbd_ctx* ctx, const rgbd_svm* m, int n) {
+    TcPlan pl;
+    return plan_tc(ctx, m, n, &pl) ? 0 : pl.bytes;
 }
 
 int score_rbf_tc_external_ws(rgbd_ctx* ctx, const rgbd_svm* m, const void* x, const float* xsq, int n,

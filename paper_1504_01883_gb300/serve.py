@@ -125,6 +125,7 @@ class ServeReport:
     batches: int = 0
     wall_s: float = 0.0
     rejections: int = 0
+    submit_s: float = 0.0  # when the caller had handed over the last frame (the library's loop)
 
     def summary(self):
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.array([np.nan])
@@ -462,6 +463,7 @@ class NativeBatchServer:
                     time.sleep(dt - 0.0003)
             by_id[self._submit(req)] = req
             collect()
+        report.submit_s = time.clock_gettime(clock) - t0
         deadline = time.monotonic() + 60.0
         while by_id:
             left = len(by_id)
