@@ -459,16 +459,20 @@ def test_tuning_changes_layout_not_results(B, ctx, orc, splits, mc):
     assert rel_score_error(s1.cpu().numpy(), s0.cpu().numpy().astype(np.float64), scale) <= 1e-5
 
 
-@pytest.mark.parametrize("dt,n,kz", [("bf16", 1, 0), ("bf16", 6, 0), ("bf16", 100, 0), ("bf16", 128, 0),
-                                     ("bf16", 37, 3), ("bf16", 5, 59), ("fp8", 12, 0), ("tf32", 9, 5),
-                                     ("bf16x3", 17, 4)])
-def test_small_batch_split_k(B, ctx, orc, dt, n, kz):
+@pytest.mark.parametrize("dt,n,kz,n_sv,C", [("bf16", 1, 0, 2000, 24), ("bf16", 6, 0, 2000, 24),
+                                            ("bf16", 100, 0, 2000, 24), ("bf16", 128, 0, 2000, 24),
+                                            ("bf16", 37, 3, 2000, 24), ("bf16", 5, 59, 2000, 24),
+                                            ("fp8", 12, 0, 2000, 24), ("tf32", 9, 5, 2000, 24),
+                                            ("bf16x3", 17, 4, 2000, 24), ("bf16", 3, 0, 100, 3),
+                                            ("bf16", 20, 0, 300, 128)])
+def test_small_batch_split_k(B, ctx, orc, dt, n, kz, n_sv, C):
     """Batches of one 128-row block split the K extent of every SV tile over several CTAs
     (automatically when the tiles alone fill few SMs; kz forces that many ranges): scores
     within the path's tolerance of the fp64 oracle, labels equal where the margin allows, and
     the same scores as the tile kernel within rounding."""
-    # 8 SV tiles, the last ragged; 64 cells: 30 FP8 k-blocks, so even FP8 has 3 K ranges
-    X, SV, a, b, gamma = _scoring_problem(300 + n + kz, n, 2000, 24, cells=64)
+    # 2000 SVs: 8 SV tiles, the last ragged (100: one partial tile; 300 with 128 classes: the
+    # widest coefficient rows); 64 cells: 30 FP8 k-blocks, so even FP8 has 3 K ranges
+    X, SV, a, b, gamma = _scoring_problem(300 + n + kz, n, n_sv, C, cells=64)
     model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype=dt)
     x, q = B.lbp_normalize_features(ctx, dev_u16(X), dt, x_scale=448.0)
     ctx.set_tuning(B.TUNE_TC_SPLITK, kz)
