@@ -1371,6 +1371,9 @@ int plan_tc(rgbd_ctx* ctx, const rgbd_svm* m, int n, TcPlan* pl, size_t ws_cap =
         const int KT = pl->passes * (m->k_pad * pl->esz / 128);
         int kz = ctx->tune_tc_splitk >= 2 ? ctx->tune_tc_splitk
                                           : (2 * pl->nt <= ctx->props.sm_count ? ctx->props.sm_count / pl->nt : 0);
+        // above 32 rows the partials' traffic (kz x n_pad x n floats, written and read back)
+        // outweighs the wider spread: half the ranges measured faster at 64 and 128 rows
+        if (ctx->tune_tc_splitk == 0 && n > 32) kz = std::max(2, kz / 2);
         kz = std::min(kz, std::max(1, KT / 8));
         if (kz >= 2) {
             pl->kpz = (KT + kz - 1) / kz;
