@@ -283,7 +283,8 @@ def main():
                          "3=2-CTA MMA, K1 threads per cell 2 or 1) instead of the autotuner, e.g. to profile "
                          "the layout a previous run chose")
     ap.add_argument("--ref-crops-per-step", type=int, default=8)
-    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision", "roi", "train"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision", "roi", "train",
+                             "small-batch"],
                     help="batch: the headline line; the others measure the remaining workloads")
     ap.add_argument("--seconds", type=float, default=10.0, help="serving: simulated seconds of arrivals")
     ap.add_argument("--serving-seconds", type=float, default=3.0,

@@ -10,6 +10,7 @@ serving    32 Poisson streams at 30 fps, 1-12 faces per frame, 8192 SVs (BF16) x
            resident: continuous batching vs the plain per-crop path, p50 / p99 frame latency.
 roi        Section 2.1's depth-space face regions for 4096 colour boxes over 256 frames.
 train      Section 2.5's classifier trained on the GPU: 64 one-vs-rest RBF SVMs on 4096 rows.
+small-batch  scoring latency of 1-128 rows against the serving model: split over K vs tile kernel.
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -482,6 +483,52 @@ def run_train(args):
                   "scoring_precision": per_mode, "status": ctx.status(clear=True)})
 
 
+# ---------------------------------------------------------------------------------------------
+def run_small_batch(args):
+    """Scoring latency of serving-sized batches (1-128 rows) against the serving model (8192
+    SVs x 15104, BF16, 64 classes): the small-batch split over K against the tile kernel
+    (RGBD_TUNE_TC_SPLITK = 1), CUDA events around each call, median of `--steps` calls after
+    `--warmup`."""
+    import torch
+    from paper_1504_01883_gb300 import _build, synth
+    from paper_1504_01883_gb300 import binding as B
+    _build.build()
+    dev = torch.device("cuda")
+    ctx = B.Context(0)
+    dim = 16 * 16 * 59
+    rng = synth.rng_for(1508 + 5)
+    sv = synth.poisson_counts(rng, 8192, dim)
+    a, b = synth.rbf_coefficients(rng, 64, 8192)
+    model = B.svm_train_data_pack(ctx, torch.from_numpy(sv.view(np.int16)).to(dev), torch.from_numpy(a).to(dev),
+                                  torch.from_numpy(b).to(dev), gamma=1.0 / dim, dtype="bf16")
+    s = torch.cuda.Stream()
+    res = {}
+    for n in (1, 6, 12, 24, 64, 128):
+        X = torch.from_numpy(synth.poisson_counts(rng, n, dim).view(np.int16)).to(dev)
+        x, q = B.lbp_normalize_features(ctx, X, "bf16")
+        sc, lb = B.svm_score(ctx, model, x, q)
+        row = {}
+        for name, knob in (("split_k", 0), ("tile_kernel", 1)):
+            ctx.set_tuning(B.TUNE_TC_SPLITK, knob)
+            ts = []
+            for i in range(args.warmup + args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                B.svm_score(ctx, model, x, q, scores=sc, labels=lb, stream=s)
+                e1.record(s)
+                e1.synchronize()
+                if i >= args.warmup:
+                    ts.append(1000.0 * e0.elapsed_time(e1))
+            row[name + "_us"] = round(float(np.median(ts)), 1)
+        ctx.set_tuning(B.TUNE_TC_SPLITK, 0)
+        res[str(n)] = row
+    status = ctx.status(clear=True)
+    model.free()
+    return _emit({"workload": "small-batch scoring: 1-128 rows x 8192 SVs x 15104 (BF16), 64 classes",
+                  "metric": "scoring latency (us, CUDA events, median)", "calls": args.steps, "rows": res,
+                  "status": status})
+
+
 def run(args):
     return {"crop": run_crop, "frame": run_frame, "precision": run_precision, "serving": run_serving,
-            "roi": run_roi, "train": run_train}[args.workload](args)
+            "roi": run_roi, "train": run_train, "small-batch": run_small_batch}[args.workload](args)

@@ -1095,7 +1095,7 @@ __global__ void __launch_bounds__(SK_WARPS * 32, 1)
 // are issued together: the kernel is a short chain of dependent L2 round trips.
 constexpr int SKE_ROWS = 16;
 constexpr int SKE_THREADS = 256;
-constexpr int SKE_CPW = 4;  // classes per warp and pass (their coefficients loaded at once)
+constexpr int SKE_CPW = 8;  // classes per warp and pass (their coefficients loaded at once)
 __global__ void __launch_bounds__(SKE_THREADS) rbf_splitk_epilogue_kernel(
     const float* __restrict__ gpart, int kz, int n_pad, int n, const float* __restrict__ xsq,
     const float* __restrict__ svsq, int n_sv, const float* __restrict__ coef, int C, int C_pad, float gamma,
@@ -1197,28 +1197,43 @@ __global__ void __launch_bounds__(SKE_THREADS) rbf_splitk_epilogue_kernel(
             s_as[idx] = t == 0 ? 0.f : __ldg(asum_tile + (size_t)t * C_pad + c);
         }
     __syncthreads();
-    // thread = (row, class): the tiles' partial sums loaded 16 at a time, then added in tile order
-    for (int idx = threadIdx.x; idx < rows * C; idx += SKE_THREADS) {
-        const int k = idx / C, c = idx - k * C;
-        const float* pp = part + (size_t)(k0 + k) * C_pad + c;
-        const size_t ts = (size_t)n * C_pad;
-        float acc = 0.f;
-        for (int t0 = 0; t0 < nt; t0 += 16) {
-            float d[16];
+    // thread = (row, class), two of them at a time: the tiles' partial sums loaded 32 at a time
+    // for both (one L2 round trip per chunk), then added in tile order
+    const size_t ts = (size_t)n * C_pad;
+    for (int i0 = threadIdx.x; i0 < rows * C; i0 += 2 * SKE_THREADS) {
+        const int i1 = i0 + SKE_THREADS;
+        const bool two = i1 < rows * C;
+        const int ka = i0 / C, ca = i0 - ka * C;
+        const int kb = two ? i1 / C : ka, cb = two ? i1 - kb * C : ca;
+        const float* pa = part + (size_t)(k0 + ka) * C_pad + ca;
+        const float* pb = part + (size_t)(k0 + kb) * C_pad + cb;
+        float acc_a = 0.f, acc_b = 0.f;
+        for (int t0 = 0; t0 < nt; t0 += 32) {
+            float da[32], db[32];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) d[j] = t0 + j < nt ? __ldcg(pp + (t0 + j) * ts) : 0.f;
+            for (int j = 0; j < 32; ++j) {
+                da[j] = t0 + j < nt ? __ldcg(pa + (t0 + j) * ts) : 0.f;
+                db[j] = (two && t0 + j < nt) ? __ldcg(pb + (t0 + j) * ts) : 0.f;
+            }
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 32; ++j) {
                 if (t0 + j < nt) {
                     const int t = t0 + j;
-                    const float as = as_fit ? s_as[t * C + c] : (t == 0 ? 0.f : __ldg(asum_tile + (size_t)t * C_pad + c));
-                    acc += d[j] + s_del[k * nt + t] * (as + d[j]);
+                    const float asa = as_fit ? s_as[t * C + ca] : (t == 0 ? 0.f : __ldg(asum_tile + (size_t)t * C_pad + ca));
+                    const float asb = as_fit ? s_as[t * C + cb] : (t == 0 ? 0.f : __ldg(asum_tile + (size_t)t * C_pad + cb));
+                    acc_a += da[j] + s_del[ka * nt + t] * (asa + da[j]);
+                    acc_b += db[j] + s_del[kb * nt + t] * (asb + db[j]);
                 }
             }
         }
-        const float sc = expf(-gamma * __ldcg(ref + k0 + k)) * (__ldg(asum + c) + acc) + __ldg(bias + c);
-        scores[(size_t)(k0 + k) * C + c] = sc;
-        if (sc_fit) s_sc[idx] = sc;
+        const float sa = expf(-gamma * __ldcg(ref + k0 + ka)) * (__ldg(asum + ca) + acc_a) + __ldg(bias + ca);
+        scores[(size_t)(k0 + ka) * C + ca] = sa;
+        if (sc_fit) s_sc[i0] = sa;
+        if (two) {
+            const float sb = expf(-gamma * __ldcg(ref + k0 + kb)) * (__ldg(asum + cb) + acc_b) + __ldg(bias + cb);
+            scores[(size_t)(k0 + kb) * C + cb] = sb;
+            if (sc_fit) s_sc[i1] = sb;
+        }
     }
     if (!labels) return;
     __syncthreads();
