@@ -48,23 +48,24 @@ struct Request {
 
 // Buffers of one batch: device rows and outputs, pinned host staging.  Two of them let one batch
 // be prepared while the other runs.
+// Each direction moves in one copy: the input block holds the batch's rects (frame = slot)
+// followed by its meta rows (stream of each frame, then the face starts), the output block its
+// scores [faces][C], then labels [faces], then identities [faces] -- offsets that depend on the
+// batch's face count.
 struct BatchBuf {
-    rgbd_rect* d_rects = nullptr;  // [max_batch_faces]: (slot, x, y, w, h)
-    int32_t* d_meta = nullptr;     // [2 n_slots + 1]: stream of each frame, then face starts
-    void* d_x = nullptr;           // normalised rows in the model's type
+    unsigned char* d_in = nullptr;   // device input block (rects, meta)
+    unsigned char* h_in = nullptr;   // pinned
+    void* d_x = nullptr;             // normalised rows in the model's type
     float* d_xsq = nullptr;
-    float* d_scores = nullptr;     // [max_batch_faces][C]
-    int32_t* d_labels = nullptr;
-    int32_t* d_ids = nullptr;
-    rgbd_rect* h_rects = nullptr;  // pinned
-    int32_t* h_meta = nullptr;
-    float* h_scores = nullptr;
-    int32_t* h_labels = nullptr;
-    int32_t* h_ids = nullptr;
-    uint32_t* h_status = nullptr;  // the context's status word after the batch
+    float* d_out = nullptr;          // device output block (scores, labels, identities)
+    float* h_out = nullptr;          // pinned
+    uint32_t* h_status = nullptr;    // the context's status word after the batch
     cudaEvent_t done = nullptr;
     bool busy = false;
 };
+size_t in_bytes(int faces, int n_slots) {
+    return sizeof(rgbd_rect) * (size_t)faces + sizeof(int32_t) * (size_t)(2 * n_slots + 1);
+}
 
 struct Batch {
     std::vector<Request> reqs;
@@ -131,49 +132,44 @@ int launch(rgbd_server* s, Batch& b) {
     const rgbd_server_config& c = s->cfg;
     const int nf = (int)b.reqs.size();
     int faces = 0;
+    for (const Request& r : b.reqs) faces += r.n;
+    b.faces = faces;
+    rgbd_rect* h_rects = reinterpret_cast<rgbd_rect*>(bb.h_in);
+    int32_t* h_meta = reinterpret_cast<int32_t*>(bb.h_in + sizeof(rgbd_rect) * (size_t)faces);
+    int at = 0;
     for (int f = 0; f < nf; ++f) {
         const Request& r = b.reqs[f];
         for (int i = 0; i < r.n; ++i) {
             rgbd_rect q = r.rects[i];
             q.frame = r.slot;
-            bb.h_rects[faces + i] = q;
+            h_rects[at + i] = q;
         }
-        bb.h_meta[f] = r.stream;
-        bb.h_meta[c.n_slots + f] = faces;
-        faces += r.n;
+        h_meta[f] = r.stream;
+        h_meta[c.n_slots + f] = at;
+        at += r.n;
         cudaError_t e = cudaStreamWaitEvent(s->compute, s->slot_ev[r.slot], 0);
         if (e != cudaSuccess) return rgbd::cuda_error(e, "rgbd_server: wait for upload");
     }
-    bb.h_meta[c.n_slots + nf] = faces;
-    b.faces = faces;
-    cudaError_t e = cudaSuccess;
-    if (faces > 0)
-        e = cudaMemcpyAsync(bb.d_rects, bb.h_rects, sizeof(rgbd_rect) * (size_t)faces, cudaMemcpyHostToDevice,
-                            s->compute);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(bb.d_meta, bb.h_meta, sizeof(int32_t) * (size_t)(2 * c.n_slots + 1),
-                            cudaMemcpyHostToDevice, s->compute);
+    h_meta[c.n_slots + nf] = faces;
+    const rgbd_rect* d_rects = reinterpret_cast<const rgbd_rect*>(bb.d_in);
+    const int32_t* d_meta = reinterpret_cast<const int32_t*>(bb.d_in + sizeof(rgbd_rect) * (size_t)faces);
+    float* d_scores = bb.d_out;
+    int32_t* d_labels = reinterpret_cast<int32_t*>(bb.d_out + (size_t)faces * s->C);
+    int32_t* d_ids = d_labels + faces;
+    cudaError_t e = cudaMemcpyAsync(bb.d_in, bb.h_in, in_bytes(faces, c.n_slots), cudaMemcpyHostToDevice, s->compute);
     if (e != cudaSuccess) return rgbd::cuda_error(e, "rgbd_server: batch upload");
     const size_t k_pad = (size_t)s->k_pad;
-    int rc = lbp_fused_features(s->ctx, s->d_grey, s->d_depth, c.n_slots, c.H, c.W, bb.d_rects, nullptr, faces,
+    int rc = lbp_fused_features(s->ctx, s->d_grey, s->d_depth, c.n_slots, c.H, c.W, d_rects, nullptr, faces,
                                 c.crop, rgbd::kCell, c.mask_mm, c.flags, nullptr, s->x_dtype, bb.d_x, (int)k_pad,
                                 c.x_scale, s->centre, bb.d_xsq, s->compute);
-    if (!rc)
-        rc = svm_score(s->ctx, s->model, bb.d_x, bb.d_xsq, faces, c.x_scale, bb.d_scores, bb.d_labels, s->compute);
+    if (!rc) rc = svm_score(s->ctx, s->model, bb.d_x, bb.d_xsq, faces, c.x_scale, d_scores, d_labels, s->compute);
     if (!rc)
         rc = rgbd_track_streams(s->ctx, s->d_state_rects, s->d_state_ids, s->d_state_count, c.n_streams, c.max_faces,
-                                nf, bb.d_meta, bb.d_meta + c.n_slots, bb.d_rects, faces, bb.d_labels, bb.d_ids,
-                                s->compute);
+                                nf, d_meta, d_meta + c.n_slots, d_rects, faces, d_labels, d_ids, s->compute);
     if (rc) return rc;
     if (faces > 0) {
-        e = cudaMemcpyAsync(bb.h_scores, bb.d_scores, sizeof(float) * (size_t)faces * s->C, cudaMemcpyDeviceToHost,
+        e = cudaMemcpyAsync(bb.h_out, bb.d_out, sizeof(float) * (size_t)faces * (s->C + 2), cudaMemcpyDeviceToHost,
                             s->compute);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(bb.h_labels, bb.d_labels, sizeof(int32_t) * (size_t)faces, cudaMemcpyDeviceToHost,
-                                s->compute);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(bb.h_ids, bb.d_ids, sizeof(int32_t) * (size_t)faces, cudaMemcpyDeviceToHost,
-                                s->compute);
         if (e != cudaSuccess) return rgbd::cuda_error(e, "rgbd_server: result read-back");
     }
     // the batch's device status flags, read back and cleared for the next batch
@@ -186,14 +182,17 @@ int launch(rgbd_server* s, Batch& b) {
 // Results of a finished batch into the callers' buffers; its slots and buffers become free.
 void finish(rgbd_server* s, Batch& b) {
     BatchBuf& bb = s->buf[b.buf];
+    const float* h_scores = bb.h_out;
+    const int32_t* h_labels = reinterpret_cast<const int32_t*>(bb.h_out + (size_t)b.faces * s->C);
+    const int32_t* h_ids = h_labels + b.faces;
     int off = 0;
     std::vector<rgbd_completion> out;
     out.reserve(b.reqs.size());
     for (const Request& r : b.reqs) {
         if (b.status == RGBD_OK && r.n > 0) {
-            memcpy(r.scores, bb.h_scores + (size_t)off * s->C, sizeof(float) * (size_t)r.n * s->C);
-            memcpy(r.labels, bb.h_labels + off, sizeof(int32_t) * (size_t)r.n);
-            if (r.ids) memcpy(r.ids, bb.h_ids + off, sizeof(int32_t) * (size_t)r.n);
+            memcpy(r.scores, h_scores + (size_t)off * s->C, sizeof(float) * (size_t)r.n * s->C);
+            memcpy(r.labels, h_labels + off, sizeof(int32_t) * (size_t)r.n);
+            if (r.ids) memcpy(r.ids, h_ids + off, sizeof(int32_t) * (size_t)r.n);
         }
         off += r.n;
         if (r.slot >= 0) s->used -= s->frame_bytes + (size_t)r.n * s->face_bytes;
@@ -294,18 +293,12 @@ void worker_main(rgbd_server* s) {
 
 void free_server(rgbd_server* s) {
     for (BatchBuf& bb : s->buf) {
-        cudaFree(bb.d_rects);
-        cudaFree(bb.d_meta);
+        cudaFree(bb.d_in);
         cudaFree(bb.d_x);
         cudaFree(bb.d_xsq);
-        cudaFree(bb.d_scores);
-        cudaFree(bb.d_labels);
-        cudaFree(bb.d_ids);
-        cudaFreeHost(bb.h_rects);
-        cudaFreeHost(bb.h_meta);
-        cudaFreeHost(bb.h_scores);
-        cudaFreeHost(bb.h_labels);
-        cudaFreeHost(bb.h_ids);
+        cudaFree(bb.d_out);
+        cudaFreeHost(bb.h_in);
+        cudaFreeHost(bb.h_out);
         cudaFreeHost(bb.h_status);
         if (bb.done) cudaEventDestroy(bb.done);
     }
@@ -378,18 +371,12 @@ int rgbd_server_create(const rgbd_svm* model, const rgbd_server_config* cfg, rgb
     dev((void**)&s->d_state_count, sizeof(int32_t) * (size_t)c.n_streams);
     if (e == cudaSuccess) e = cudaMemset(s->d_state_count, 0, sizeof(int32_t) * (size_t)c.n_streams);
     for (BatchBuf& bb : s->buf) {
-        dev((void**)&bb.d_rects, sizeof(rgbd_rect) * nb);
-        dev((void**)&bb.d_meta, sizeof(int32_t) * (2 * ns + 1));
+        dev((void**)&bb.d_in, in_bytes(c.max_batch_faces, c.n_slots));
         dev(&bb.d_x, x_elem_bytes(s->x_dtype) * nb * (size_t)s->k_pad);
         dev((void**)&bb.d_xsq, sizeof(float) * nb);
-        dev((void**)&bb.d_scores, sizeof(float) * nb * s->C);
-        dev((void**)&bb.d_labels, sizeof(int32_t) * nb);
-        dev((void**)&bb.d_ids, sizeof(int32_t) * nb);
-        pin((void**)&bb.h_rects, sizeof(rgbd_rect) * nb);
-        pin((void**)&bb.h_meta, sizeof(int32_t) * (2 * ns + 1));
-        pin((void**)&bb.h_scores, sizeof(float) * nb * s->C);
-        pin((void**)&bb.h_labels, sizeof(int32_t) * nb);
-        pin((void**)&bb.h_ids, sizeof(int32_t) * nb);
+        dev((void**)&bb.d_out, sizeof(float) * nb * (s->C + 2));
+        pin((void**)&bb.h_in, in_bytes(c.max_batch_faces, c.n_slots));
+        pin((void**)&bb.h_out, sizeof(float) * nb * (s->C + 2));
         pin((void**)&bb.h_status, sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bb.done, cudaEventDisableTiming);
     }
