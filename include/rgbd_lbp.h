@@ -316,7 +316,11 @@ int rgbd_svm_centre(const rgbd_svm* model, const float** centre);
  *   scores  float [n][n_classes]: S_c = sum_i a_ci exp(-gamma |x - sv_i|^2) + b_c
  *           (RBF) or w_c . x + b_c (linear).
  *   labels  NULL or int32 [n]: argmax_c S_c, lowest index on ties.
- * Uses context workspace (partial sums), grown on demand.
+ * Uses context workspace (partial sums), grown on demand.  Tensor-core models
+ * score up to 128 rows by splitting the SV tiles' K extent over several CTAs
+ * (two launches, the second a programmatic dependent of the first) when the
+ * tiles alone would occupy few SMs (RGBD_TUNE_TC_SPLITK); larger batches by SV
+ * tiles.  The two paths round differently within the model type's tolerance.
  * Errors: RGBD_ERR_ARG, RGBD_ERR_UNSUPPORTED, RGBD_ERR_NOMEM, RGBD_ERR_CUDA. */
 int svm_score(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const float* xsq, int n,
               float x_scale, float* scores, int32_t* labels, void* stream);
