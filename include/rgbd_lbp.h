@@ -438,7 +438,8 @@ int svm_score_noalloc(rgbd_ctx* ctx, const rgbd_svm* model, const void* x, const
  * arrive while a batch is on the GPU are uploaded on a copy stream and form the next batch
  * (all their faces in one fused launch and one scoring launch), so uploads overlap compute and
  * batches follow each other without a gap.  While work is in flight the worker polls its
- * events (spinning with yields: one host core for latency); idle, it sleeps until a submission.
+ * events (spinning with yields: one host core for latency); out of work, it keeps polling for
+ * idle_spin_us, then sleeps until a submission.
  * The server owns its own context (workspace, face queues); the model must outlive it and is
  * only read. */
 typedef struct rgbd_server_config {
@@ -451,6 +452,10 @@ typedef struct rgbd_server_config {
     int32_t n_streams;        /* camera streams tracked, 1..65536 */
     int32_t max_faces;        /* faces remembered per stream for tracking, 1..256 */
     float x_scale;            /* FP8 per-tensor scale of the rows (FP8 models), else ignored */
+    int32_t idle_spin_us;     /* 0..1000000: how long the worker keeps polling for submissions
+                                 after it runs out of work before it sleeps (0: at once).  A
+                                 sleeping worker wakes through the operating system's scheduler,
+                                 tens of microseconds added to the next frame's latency */
 } rgbd_server_config;
 
 /* One finished request, as returned by rgbd_server_poll. */

@@ -467,7 +467,7 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int32), ("max_batch_faces", ctypes.c_int32), ("H", ctypes.c_int32),
                 ("W", ctypes.c_int32), ("crop", ctypes.c_int32), ("mask_mm", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("n_streams", ctypes.c_int32), ("max_faces", ctypes.c_int32),
-                ("x_scale", ctypes.c_float)]
+                ("x_scale", ctypes.c_float), ("idle_spin_us", ctypes.c_int32)]
 
 
 class Completion(ctypes.Structure):
@@ -485,8 +485,9 @@ class NativeServer:
     until their request is polled."""
 
     def __init__(self, model, H, W, n_streams, n_slots=96, max_batch_faces=2048, crop=128, mask_mm=150, flags=0,
-                 max_faces=16, x_scale=448.0):
-        cfg = ServerConfig(n_slots, max_batch_faces, H, W, crop, mask_mm, flags, n_streams, max_faces, x_scale)
+                 max_faces=16, x_scale=448.0, idle_spin_us=2000):
+        cfg = ServerConfig(n_slots, max_batch_faces, H, W, crop, mask_mm, flags, n_streams, max_faces, x_scale,
+                           idle_spin_us)
         h = ctypes.c_void_p()
         _check(lib().rgbd_server_create(model.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

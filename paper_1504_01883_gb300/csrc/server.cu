@@ -107,6 +107,7 @@ struct rgbd_server {
     std::deque<rgbd_completion> done;  // finished, not yet polled
     std::atomic<int> pending{0};       // submitted and not finished
     bool stop = false;
+    std::atomic<bool> stopping{false};  // stop, readable without the lock (the idle poll)
     uint64_t next_id = 1;
     std::atomic<uint64_t> frames{0}, faces{0}, batches{0}, waits{0};
     std::thread worker;
@@ -224,6 +225,15 @@ void worker_main(rgbd_server* s) {
     std::deque<Batch> inflight;
     for (;;) {
         bool progress = false;
+        if (waiting.empty() && admitted.empty() && inflight.empty() && s->cfg.idle_spin_us > 0) {
+            // out of work: poll for a submission for a while before sleeping on the condition
+            // variable (a sleeping thread wakes through the scheduler, which adds tens of
+            // microseconds to the next frame)
+            const double t_idle = now_s(), spin = 1e-6 * s->cfg.idle_spin_us;
+            while (s->pending.load(std::memory_order_acquire) == 0 && !s->stopping.load(std::memory_order_acquire) &&
+                   now_s() - t_idle < spin)
+                std::this_thread::yield();
+        }
         {
             std::unique_lock<std::mutex> lk(s->mu);
             if (waiting.empty() && admitted.empty() && inflight.empty() && s->incoming.empty()) {
@@ -339,6 +349,8 @@ int rgbd_server_create(const rgbd_svm* model, const rgbd_server_config* cfg, rgb
     if (c.n_streams < 1 || c.n_streams > 65536 || c.max_faces < 1 || c.max_faces > 256)
         return set_error(RGBD_ERR_ARG, "rgbd_server_create: n_streams %d (1..65536), max_faces %d (1..256)",
                          c.n_streams, c.max_faces);
+    if (c.idle_spin_us < 0 || c.idle_spin_us > 1000000)
+        return set_error(RGBD_ERR_ARG, "rgbd_server_create: idle_spin_us %d (0..1000000)", c.idle_spin_us);
     if (model->dtype == RGBD_DT_FP8 && !(c.x_scale > 0.f && c.x_scale < 1e30f))
         return set_error(RGBD_ERR_ARG, "rgbd_server_create: FP8 models need x_scale > 0");
     rgbd_server* s = new (std::nothrow) rgbd_server();
@@ -481,6 +493,7 @@ int rgbd_server_destroy(rgbd_server* s) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        s->stopping.store(true, std::memory_order_release);
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
