@@ -280,7 +280,8 @@ def main():
                          "kernel overlaps step i's scoring)")
     ap.add_argument("--tune", default=None, metavar="CTAS,SPLITS,PAIRING[,SHAPE]",
                     help="fixed launch layout (K1 CTAs/SM, scoring splits, CTA pairing 2=none "
-                         "3=2-CTA MMA, K1 threads per cell 2 or 1) instead of the autotuner, e.g. to profile "
+                         "3=2-CTA MMA, K1 tile shape 2=half cells 1=cells 3=quarter cells) instead of the autotuner, "
+                         "e.g. to profile "
                          "the layout a previous run chose")
     ap.add_argument("--ref-crops-per-step", type=int, default=8)
     ap.add_argument("--workload", default="batch", choices=["batch", "serving", "crop", "frame", "precision", "roi", "train",

@@ -138,7 +138,8 @@ int rgbd_ctx_status(rgbd_ctx* ctx, uint32_t* flags, int clear);
  *   RGBD_TUNE_LBP_SHAPE         fused-kernel tile shape: 0 = default (2), 1 = one thread
  *                               per 8 x 8 cell (crops 64 and 128; CTAs of (crop/8)^2
  *                               threads), 2 = one thread per 4 x 8 half cell (CTAs of
- *                               2 (crop/8)^2 threads)
+ *                               2 (crop/8)^2 threads), 3 = one thread per 4 x 4 quarter
+ *                               cell (crops 64 and 128; CTAs of 4 (crop/8)^2 threads)
  *   RGBD_TUNE_TC_PAIRING        CTA pairing of 128-row blocks in tensor-core scoring:
  *                               0 = default (3), 2 = no pairing, 3 = each pair runs one
  *                               256-row MMA (tcgen05 cta_group::2, each CTA holding half of

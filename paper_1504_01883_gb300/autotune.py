@@ -5,8 +5,9 @@ candidate settings of the context's tuning knobs and keeps the fastest:
 
   K1  the fused kernel's tile shape and resident CTAs per SM: one CTA per face works on a
       128 x 128 crop laid out as 16 x 16 cells of 8 x 8 pixels, with either one thread per
-      4 x 8 half cell (512 threads, 64 registers) or one thread per cell (256 threads, up to
-      128 registers), and one or two such CTAs in flight per SM;
+      4 x 8 half cell (512 threads, 64 registers), one thread per cell (256 threads, up to
+      128 registers) or one per 4 x 4 quarter cell (1024 threads, one CTA per SM), and one or
+      two such CTAs in flight per SM;
   K2  how many SV-tile ranges ("splits") each 128-row block of the tensor-core scoring
       kernel is cut into (the row x SV tiling across SMs), and whether CTA pairs run one
       256-row MMA (tcgen05 cta_group::2) or every CTA runs its own 128-row MMA.
@@ -25,7 +26,7 @@ import torch
 
 from . import binding as B
 
-CACHE_VERSION = 3  # bumped whenever the set of knobs changes
+CACHE_VERSION = 4  # bumped whenever the set of knobs changes
 CACHE_PATH = os.environ.get("RGBD_TUNE_CACHE",
                             os.path.join(os.path.expanduser("~"), ".cache", "rgbd_lbp_gb300", "tune.json"))
 
@@ -35,7 +36,7 @@ class Tuning:
     lbp_ctas_per_sm: int = 0
     tc_splits: int = 0
     tc_pairing: int = 0
-    lbp_shape: int = 0   # fused-kernel threads per cell (2: half cells, 1: whole cells; 0 = default)
+    lbp_shape: int = 0   # fused-kernel threads per cell (2: half cells, 1: whole cells, 3: quarter cells; 0 = default)
 
     def apply(self, ctx):
         ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, self.lbp_ctas_per_sm)
@@ -45,7 +46,7 @@ class Tuning:
 
 
 PAIRING_NAMES = {2: "single", 3: "pair"}
-SHAPE_NAMES = {1: "cell", 2: "halfcell"}
+SHAPE_NAMES = {1: "cell", 2: "halfcell", 3: "quartercell"}
 
 
 def _time(fn, stream, reps=3):
@@ -111,8 +112,8 @@ def tune(ctx, key, stage1, stage2, n_rows, n_sv, stream, use_cache=True, tensor_
     best = Tuning()
     # K1: tile shape x CTAs per SM
     best_ms = None
-    for shape in (2, 1):
-        for c in (2, 1):
+    for shape in (2, 1, 3):
+        for c in ((2, 1) if shape != 3 else (1,)):  # a 1024-thread CTA fills an SM's registers
             ctx.set_tuning(B.TUNE_LBP_SHAPE, shape)
             ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, c)
             ms = _time(stage1, stream)

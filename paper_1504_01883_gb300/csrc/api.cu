@@ -148,7 +148,7 @@ int rgbd_ctx_set_tuning(rgbd_ctx* ctx, int key, int value) {
             ctx->tune_tc_splits = value;
             return RGBD_OK;
         case RGBD_TUNE_LBP_SHAPE:
-            CHECK_ARG(value <= 2, "rgbd_ctx_set_tuning: fused-kernel shape %d (0, 1 or 2)", value);
+            CHECK_ARG(value <= 3, "rgbd_ctx_set_tuning: fused-kernel shape %d (0..3)", value);
             ctx->tune_lbp_shape = value;
             return RGBD_OK;
         case RGBD_TUNE_TC_SPLITK:

@@ -43,7 +43,7 @@ struct rgbd_ctx {
     int tune_lbp_ctas_per_sm = 0;  // 0 = occupancy limit
     int tune_tc_splits = 0;        // 0 = cost model
     int tune_tc_pairing = 0;       // CTA pairing: 0 = auto, 2 = none, 3 = 2-CTA MMA pairs
-    int tune_lbp_shape = 0;        // fused-kernel threads per cell: 0 = auto (2), 1 = one, 2 = two
+    int tune_lbp_shape = 0;        // fused-kernel threads per cell: 0 = auto, 1 = one, 2 = two, 3 = four
     int tune_tc_splitk = 0;        // K ranges of one-block scoring: 0 = auto, 1 = off, >= 2 forced
     uint32_t* d_status = nullptr;  // device status word, followed by kFaceCounters face-queue counters
     uint32_t* d_counters = nullptr;

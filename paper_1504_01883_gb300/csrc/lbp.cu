@@ -117,8 +117,9 @@ __device__ __forceinline__ int qbf_slot(int i) { return i ^ (((i >> 7) & 31) << 
 __device__ __forceinline__ uint32_t qbf_slot2(uint32_t w) { return w ^ ((w >> 6) & 0x003E003Eu); }
 
 // Tile shape of the fused kernel: TPC threads per 8 x 8 cell (2: one per 4 x 8 half cell, 1: one
-// per cell), so a CTA of NT = TPC (S/8)^2 threads works on one face; each thread resamples IPT
-// groups of 4 crop pixels.
+// per cell, 4: one per 4 x 4 quarter cell), so a CTA of NT = TPC (S/8)^2 threads works on one
+// face; each thread resamples IPT groups of 4 crop pixels.  Four threads per cell make 1024-thread
+// CTAs for 128 x 128 crops: one per SM, twice the warps on a face.
 template <int S, int TPC = 2>
 struct Cfg {
     static constexpr int G = S / 8;          // cells per side
@@ -127,8 +128,10 @@ struct Cfg {
     static constexpr int IPT = S * S / 4 / NT;  // 4-pixel groups per thread
     static constexpr int DIM = G * G * kBins;
     static constexpr int HW = 15;            // histogram words per thread (60 bins / 4)
-    static constexpr int MINB = (S == 128) ? 2 : 1;
-    static_assert(TPC == 1 || TPC == 2, "one or two threads per cell");
+    static constexpr int MINB = (S == 128 && TPC <= 2) ? 2 : 1;
+    static constexpr int RPT = TPC == 4 ? 4 : 8;        // cell rows a thread walks in P5
+    static constexpr int WPT = (HW + TPC - 1) / TPC;    // histogram words a thread stages in P6
+    static_assert(TPC == 1 || TPC == 2 || TPC == 4, "one, two or four threads per cell");
 };
 
 template <int S, int TPC = 2>
@@ -547,17 +550,19 @@ __global__ void __launch_bounds__(Cfg<S, TPC>::NT, Cfg<S, TPC>::MINB) lbp_fused_
 #pragma unroll
         for (int w = 0; w < C::HW; ++w) sm.hist[w * NT + tid] = 0;  // (the depths are no longer needed)
         {
-            // the thread's half cell (TPC = 2), or both halves of its cell in turn (TPC = 1)
+            // the thread's half cell (TPC = 2), both halves of its cell in turn (TPC = 1), or a
+            // quarter: the upper or lower four rows of a half (TPC = 4)
             const int c = tid / TPC;
             const int cy = c / G, cx = c - cy * G;
-            const int r0 = 8 * cy;
+            const int r0 = 8 * cy + (TPC == 4 ? 4 * ((tid >> 1) & 1) : 0);
+            constexpr int RPT = C::RPT;
             const uint32_t* GW = sm.img;
             const uint32_t* MW = sm.img + MW_OFF;
             uint32_t nvalid = 0;
             uint8_t* hb_t = reinterpret_cast<uint8_t*>(sm.hist) + 4 * tid;  // this thread's counters
 #pragma unroll 1
-            for (int hh = 0; hh < 2 / TPC; ++hh) {
-            const int h = TPC == 2 ? (tid & 1) : hh;
+            for (int hh = 0; hh < (TPC == 1 ? 2 : 1); ++hh) {
+            const int h = TPC == 1 ? hh : (tid & 1);
             const int wc = 2 * cx + h;
             const bool le = wc == 0, re = wc == SW - 1;
             const int wl = le ? wc : wc - 1, wr = re ? wc : wc + 1;
@@ -586,7 +591,7 @@ __global__ void __launch_bounds__(Cfg<S, TPC>::NT, Cfg<S, TPC>::MINB) lbp_fused_
                 row3g(r0 - 1, gUL, gUC, gUR);
                 row3g(r0, gCL, gCC, gCR);
 #pragma unroll 2
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < RPT; ++i) {
                     row3g(r0 + i + 1, gDL, gDC, gDR);
                     const uint32_t mC = MW[(r0 + i) * SW + wc];
                     // an invalid centre compares as grey 255, so no neighbour is greater and its
@@ -610,7 +615,7 @@ __global__ void __launch_bounds__(Cfg<S, TPC>::NT, Cfg<S, TPC>::MINB) lbp_fused_
             row3g(r0, gCL, gCC, gCR);
             row3(MW, r0, mCL, mCC, mCR);
 #pragma unroll 2
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < RPT; ++i) {
                 row3g(r0 + i + 1, gDL, gDC, gDR);
                 row3(MW, r0 + i + 1, mDL, mDC, mDR);
                 const uint32_t NM = 0x80808080u;
@@ -644,17 +649,22 @@ __global__ void __launch_bounds__(Cfg<S, TPC>::NT, Cfg<S, TPC>::MINB) lbp_fused_
         // ---- P6: each cell's histogram (the sum of its two halves) into a uint16 staging row
         uint16_t* stg = reinterpret_cast<uint16_t*>(sm.img);
         {
-            // TPC = 2: the two threads of a cell split its words; TPC = 1: one thread per cell
-            const int c = tid / TPC, h = TPC == 2 ? (tid & 1) : 0;
-            const uint32_t nv = TPC == 2 ? sm.cnt[2 * c] + sm.cnt[2 * c + 1] : sm.cnt[c];
+            // TPC = 2: the two threads of a cell split its words; TPC = 1: one thread per cell;
+            // TPC = 4: four threads split them (C::WPT each) and add the four partial histograms
+            // byte by byte (a byte holds at most 64 counts in all)
+            const int c = tid / TPC, h = TPC == 1 ? 0 : (tid & (TPC - 1));
+            uint32_t nv = TPC == 1 ? sm.cnt[c] : sm.cnt[TPC * c] + sm.cnt[TPC * c + 1];
+            if (TPC == 4) nv += sm.cnt[TPC * c + 2] + sm.cnt[TPC * c + 3];
             if (h == 0) {
                 sm.nvf[c] = (float)nv;
                 sm.rcp[c] = nv ? __frcp_rn((float)nv) : 0.f;
             }
-            const int w0 = h ? 8 : 0, w1 = (h || TPC == 1) ? C::HW : 8;
+            const int w0 = TPC == 4 ? h * C::WPT : (h ? 8 : 0);
+            const int w1 = TPC == 4 ? min(C::HW, w0 + C::WPT) : ((h || TPC == 1) ? C::HW : 8);
 #pragma unroll 1  // rolled: 0.7 % faster than the compiler's unrolling
             for (int w = w0; w < w1; ++w) {
-                uint32_t s = TPC == 2 ? sm.hist[w * NT + 2 * c] + sm.hist[w * NT + 2 * c + 1] : sm.hist[w * NT + c];
+                uint32_t s = TPC == 1 ? sm.hist[w * NT + c] : sm.hist[w * NT + TPC * c] + sm.hist[w * NT + TPC * c + 1];
+                if (TPC == 4) s += sm.hist[w * NT + TPC * c + 2] + sm.hist[w * NT + TPC * c + 3];
                 if (masked_grey && w == 0) s -= 64u - nv;  // the invalid centres counted as code 0
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -1264,13 +1274,19 @@ int launch_lbp_fused(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: 0-255 histogram launch");
         return RGBD_OK;
     }
-    // tile shape: one thread per cell (tuning value 1, crops 64 and 128), else per half cell
-    const bool per_cell = ctx->tune_lbp_shape == 1;
+    // tile shape (crops 64 and 128): one thread per cell (tuning value 1), per half cell (2, the
+    // default), per quarter cell (3: 1024-thread CTAs, measured 7 % slower even when every face
+    // has an SM of its own, and 50 % slower on full batches)
+    const int shape = ctx->tune_lbp_shape == 0 ? 2 : ctx->tune_lbp_shape;
     switch (a.crop) {
         case 32: return launch_fused_t<32, 2>(ctx, a, s);
-        case 64: return per_cell ? launch_fused_t<64, 1>(ctx, a, s) : launch_fused_t<64, 2>(ctx, a, s);
+        case 64:
+            return shape == 1 ? launch_fused_t<64, 1>(ctx, a, s)
+                              : (shape == 3 ? launch_fused_t<64, 4>(ctx, a, s) : launch_fused_t<64, 2>(ctx, a, s));
         case 96: return launch_fused_t<96, 2>(ctx, a, s);
-        case 128: return per_cell ? launch_fused_t<128, 1>(ctx, a, s) : launch_fused_t<128, 2>(ctx, a, s);
+        case 128:
+            return shape == 1 ? launch_fused_t<128, 1>(ctx, a, s)
+                              : (shape == 3 ? launch_fused_t<128, 4>(ctx, a, s) : launch_fused_t<128, 2>(ctx, a, s));
         default:
             return set_error(RGBD_ERR_UNSUPPORTED, "lbp_fused_features: crop %d (32, 64, 96 or 128)", a.crop);
     }

@@ -130,13 +130,14 @@ def test_lbp_option_flags(B, ctx, orc, flags):
 @pytest.mark.parametrize("crop", [64, 128])
 @pytest.mark.parametrize("flags", [0, 1, 2])
 def test_tile_shapes_bit_exact(B, ctx, orc, crop, flags):
-    """Both tile shapes of the fused kernel (one thread per cell, one per half cell), one and two
-    CTAs per SM: features bit-exact with the oracle, and the same normalised rows and norms."""
+    """Every tile shape of the fused kernel (one thread per cell, per half cell, per quarter
+    cell), one and two CTAs per SM: features bit-exact with the oracle, and the same normalised
+    rows and norms."""
     g, d, r = synth.frames_with_rects(70 + crop + flags, 3, 7, 40, 256, H=240, W=320)
     want = orc.features_batch(g, d, r, crop, flags=flags)
     rows = {}
     try:
-        for shape in (1, 2):
+        for shape in (1, 2, 3):
             for ctas in (1, 2):
                 ctx.set_tuning(B.TUNE_LBP_SHAPE, shape)
                 ctx.set_tuning(B.TUNE_LBP_CTAS_PER_SM, ctas)
@@ -155,10 +156,12 @@ def test_tile_shapes_bit_exact(B, ctx, orc, crop, flags):
 
 
 @pytest.mark.parametrize("crop", [64, 128])
-def test_tile_shapes_on_edge_cases_precut_crops_and_affine(B, ctx, orc, crop):
-    """One thread per cell on the edge frames (all-hole faces, off-frame and bad rects), on
-    pre-cut crops (no rects) and through the general affine path: bit-exact with the oracle."""
-    ctx.set_tuning(B.TUNE_LBP_SHAPE, 1)
+@pytest.mark.parametrize("shape", [1, 2, 3])
+def test_tile_shapes_on_edge_cases_precut_crops_and_affine(B, ctx, orc, crop, shape):
+    """Each tile shape (one thread per cell, per half cell, per quarter cell) on the edge frames
+    (all-hole faces, off-frame and bad rects), on pre-cut crops (no rects) and through the general
+    affine path: bit-exact with the oracle."""
+    ctx.set_tuning(B.TUNE_LBP_SHAPE, shape)
     try:
         g, d, r = _edge_frames()
         want = orc.features_batch(g, d, r, crop)
