@@ -462,13 +462,13 @@ def test_tuning_changes_layout_not_results(B, ctx, orc, splits, mc):
     assert rel_score_error(s1.cpu().numpy(), s0.cpu().numpy().astype(np.float64), scale) <= 1e-5
 
 
-@pytest.mark.parametrize("dt,n,kz,n_sv,C", [("bf16", 1, 0, 2000, 24), ("bf16", 6, 0, 2000, 24),
-                                            ("bf16", 100, 0, 2000, 24), ("bf16", 128, 0, 2000, 24),
-                                            ("bf16", 37, 3, 2000, 24), ("bf16", 5, 59, 2000, 24),
-                                            ("fp8", 12, 0, 2000, 24), ("tf32", 9, 5, 2000, 24),
-                                            ("bf16x3", 17, 4, 2000, 24), ("bf16", 3, 0, 100, 3),
-                                            ("bf16", 20, 0, 300, 128)])
-def test_small_batch_split_k(B, ctx, orc, dt, n, kz, n_sv, C):
+@pytest.mark.parametrize("dt,n,kz,n_sv,C,centred", [
+    ("bf16", 1, 0, 2000, 24, False), ("bf16", 6, 0, 2000, 24, False), ("bf16", 100, 0, 2000, 24, False),
+    ("bf16", 128, 0, 2000, 24, False), ("bf16", 37, 3, 2000, 24, False), ("bf16", 5, 59, 2000, 24, False),
+    ("fp8", 12, 0, 2000, 24, False), ("tf32", 9, 5, 2000, 24, False), ("bf16x3", 17, 4, 2000, 24, False),
+    ("bf16", 3, 0, 100, 3, False), ("bf16", 20, 0, 300, 128, False), ("bf16", 6, 0, 2000, 24, True),
+    ("fp8", 12, 0, 2000, 24, True)])
+def test_small_batch_split_k(B, ctx, orc, dt, n, kz, n_sv, C, centred):
     """Batches of one 128-row block split the K extent of every SV tile over several CTAs
     (automatically when the tiles alone fill few SMs; kz forces that many ranges): scores
     within the path's tolerance of the fp64 oracle, labels equal where the margin allows, and
@@ -476,8 +476,8 @@ def test_small_batch_split_k(B, ctx, orc, dt, n, kz, n_sv, C):
     # 2000 SVs: 8 SV tiles, the last ragged (100: one partial tile; 300 with 128 classes: the
     # widest coefficient rows); 64 cells: 30 FP8 k-blocks, so even FP8 has 3 K ranges
     X, SV, a, b, gamma = _scoring_problem(300 + n + kz, n, n_sv, C, cells=64)
-    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype=dt)
-    x, q = B.lbp_normalize_features(ctx, dev_u16(X), dt, x_scale=448.0)
+    model = B.svm_train_data_pack(ctx, dev_u16(SV), dev_f32(a), dev_f32(b), gamma=gamma, dtype=dt, centred=centred)
+    x, q = B.lbp_normalize_features(ctx, dev_u16(X), dt, x_scale=448.0, x_centre=model if centred else None)
     ctx.set_tuning(B.TUNE_TC_SPLITK, kz)
     try:
         s, lab = B.svm_score(ctx, model, x, q, x_scale=448.0)
@@ -491,7 +491,7 @@ def test_small_batch_split_k(B, ctx, orc, dt, n, kz, n_sv, C):
     scale = rbf_error_scale(x64, sv64, a, b, gamma)
     err = rel_score_error(s.cpu().numpy(), ref, scale)
     bound = {"tf32": 2e-5, "bf16": 5e-5, "fp8": 1e-3, "bf16x3": 1e-8}[dt]
-    print(f"{dt} n {n} kz {kz}: rel err {err:.3e}")
+    print(f"{dt}{' centred' if centred else ''} n {n} kz {kz}: rel err {err:.3e}")
     assert err <= bound, err
     assert rel_score_error(s.cpu().numpy(), s_tile.cpu().numpy().astype(np.float64), scale) <= 2 * bound
     srt = np.sort(ref, axis=1)
