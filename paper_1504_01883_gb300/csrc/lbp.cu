@@ -1250,11 +1250,14 @@ int launch_fused_t(rgbd_ctx* ctx, const LbpArgs& a, cudaStream_t s) {
     }
     const int per_sm = ctx->tune_lbp_ctas_per_sm > 0 ? std::min(ctx->tune_lbp_ctas_per_sm, blocks_per_sm) : blocks_per_sm;
     const int grid = (int)std::min<long long>((long long)a.n, (long long)per_sm * ctx->props.sm_count);
-    if (a.face_counter) {
-        cudaError_t e = cudaMemsetAsync(a.face_counter, 0, sizeof(uint32_t), s);
+    LbpArgs la = a;
+    if (grid >= a.n) {
+        la.face_counter = nullptr;  // one face per CTA: no queue, and no reset launch for it
+    } else if (la.face_counter) {
+        cudaError_t e = cudaMemsetAsync(la.face_counter, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: face queue reset");
     }
-    lbp_fused_kernel<S, TPC><<<grid, Cfg<S, TPC>::NT, smem, s>>>(a);
+    lbp_fused_kernel<S, TPC><<<grid, Cfg<S, TPC>::NT, smem, s>>>(la);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "lbp_fused_features: launch");
     return RGBD_OK;
