@@ -117,13 +117,15 @@ namespace {
 
 using rgbd::set_error;
 
-// Copies a frame into its slot on the copy stream and marks the slot's event.
-int upload(rgbd_server* s, const Request& r) {
+// Copies a frame into its slot on `st` and marks the slot's event: the copy stream while a batch
+// runs (the upload overlaps it), the compute stream when the GPU is idle (the batch's kernels then
+// follow the copy in stream order, without a wait on another stream's event).
+int upload(rgbd_server* s, const Request& r, cudaStream_t st) {
     const size_t plane = (size_t)s->cfg.H * s->cfg.W;
-    cudaError_t e = cudaMemcpyAsync(s->d_grey + (size_t)r.slot * plane, r.grey, plane, cudaMemcpyHostToDevice, s->copy);
+    cudaError_t e = cudaMemcpyAsync(s->d_grey + (size_t)r.slot * plane, r.grey, plane, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->d_depth + (size_t)r.slot * plane, r.depth, 2 * plane, cudaMemcpyHostToDevice, s->copy);
-    if (e == cudaSuccess) e = cudaEventRecord(s->slot_ev[r.slot], s->copy);
+        e = cudaMemcpyAsync(s->d_depth + (size_t)r.slot * plane, r.depth, 2 * plane, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->slot_ev[r.slot], st);
     return e == cudaSuccess ? RGBD_OK : rgbd::cuda_error(e, "rgbd_server: upload");
 }
 
@@ -266,7 +268,7 @@ void worker_main(rgbd_server* s) {
             r.slot = s->free_slots.back();
             s->free_slots.pop_back();
             if (r.waited) s->waits++;
-            const int rc = upload(s, r);
+            const int rc = upload(s, r, inflight.empty() ? s->compute : s->copy);
             if (rc) {  // reported through the batch that carries it
                 Batch bad;
                 bad.reqs.push_back(r);
